@@ -1,0 +1,307 @@
+"""Throughput of one MUFFIN primal-dual pass (Algorithm 1) over a whole cube.
+
+Default workload: the 512 x 512 x 256 cube (200 sources, 10% point-like,
+128 antennas, IUWT 5 scales, generation 1, mu_s = 0.25, mu_lambda = 3, step
+sizes from the power method and Condat's rule), FP32 iterates.  A step is one
+pass of Algorithm 1 over the cube; the metric is voxel-iterations per second.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl muffin|reference]
+
+Under torchrun each rank solves its own cube (seed + rank): weak scaling, no
+collective on the data path; the step time is the max over ranks.
+--impl reference times the FP64 oracle on the host cores instead (rank 0 only).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "voxel-iter/s"
+WORKLOAD = "512x512x256 cube, 200 sources (10% point), 128 antennas, IUWT J=5 gen1, mu_s=0.25, mu_l=3"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=100)
+    ap.add_argument("--warmup", type=int, default=10)
+    ap.add_argument("--impl", default="muffin", choices=["muffin", "reference"])
+    ap.add_argument("--config", default="D")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-ttt", action="store_true")
+    return ap.parse_args()
+
+
+# ------------------------------------------------------------------ clocks during the timed region
+class ClockSampler:
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.lines: list[str] = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except OSError:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *exc):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self) -> dict:
+        sm, smax, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 8:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                smax = float(parts[1])
+            except ValueError:
+                continue
+            for name, flag in zip(names, parts[4:8]):
+                if flag.lower().startswith("active"):
+                    reasons.add(name)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": smax, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ------------------------------------------------------------------ oracle timing (host cores)
+ORACLE_SNIPPET = r"""
+import json, sys, time
+sys.path.insert(0, {root!r})
+import numpy as np
+from oracle import muffin_oracle as mo
+from paper_1602_08847_gb300 import synth
+cfg = synth.CONFIGS[{cfg!r}]
+cfg = synth.CubeConfig(**{{**cfg.as_dict(), "nchan": {nchan}}})
+cube = synth.make_cube(cfg)
+p = mo.make_problem(cube.dirty, cube.psf, cfg.nscales, gen=1, mu_s=0.25, mu_l=3.0, tau=1e-3)
+s = mo.zero_state(p)
+s = mo.iterate(p, s, 1)
+times = []
+for _ in range({steps}):
+    t0 = time.perf_counter(); s = mo.iterate(p, s, 1); times.append(time.perf_counter() - t0)
+print(json.dumps({{"times": times, "voxels": cfg.n * cfg.n * cfg.nchan}}))
+"""
+
+
+def oracle_time(cfg_name: str, nchan: int, steps: int) -> dict:
+    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1")
+    code = ORACLE_SNIPPET.format(root=ROOT, cfg=cfg_name, nchan=nchan, steps=steps)
+    r = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, env=env)
+    if r.returncode != 0:
+        raise RuntimeError(r.stderr[-2000:])
+    out = json.loads(r.stdout.strip().splitlines()[-1])
+    t = sum(out["times"])
+    return {"value": out["voxels"] * len(out["times"]) / t, "seconds": t, "steps": len(out["times"]),
+            "voxels": out["voxels"]}
+
+
+def reference_arm(args, rank: int) -> None:
+    if rank != 0:
+        return
+    from paper_1602_08847_gb300 import synth
+    cfg = synth.CONFIGS[args.config]
+    nchan = 8
+    res = oracle_time(args.config, nchan, max(args.steps, 1))
+    sample = (f"{cfg.n}x{cfg.n}x{nchan} slice of the workload (same N, J, sources, antennas; first {nchan} "
+              f"channels), {res['steps']} passes after 1 untimed, numpy FP64, 1 thread")
+    line = {"impl": "reference", "metric": METRIC, "value": res["value"], "unit": METRIC, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * res["seconds"] / res["steps"],
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "sample": sample},
+            "cpu_baseline": {"value": res["value"], "unit": METRIC, "cores": 1, "kind": "oracle", "sample": sample},
+            "e2e": {"value": res["value"], "unit": METRIC, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ------------------------------------------------------------------ GPU arm
+def main():
+    args = parse()
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        reference_arm(args, rank)
+        return
+
+    import numpy as np
+    import torch
+    from paper_1602_08847_gb300 import synth
+    from paper_1602_08847_gb300.muffin import Muffin, solve
+
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    def barrier():
+        if dist:
+            dist.barrier()
+
+    def max_over_ranks(v: float) -> float:
+        if not dist:
+            return v
+        t = torch.tensor([v], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        return float(t.item())
+
+    cfg = synth.CONFIGS[args.config]
+    cube = synth.make_cube(cfg, seed=cfg.seed + rank)
+    L, n = cfg.nchan, cfg.n
+    voxels = L * n * n
+    kw = dict(nscales=cfg.nscales, gen=1, mu_s=0.25, mu_l=3.0)
+    m = Muffin(torch.from_numpy(cube.dirty).cuda(), torch.from_numpy(cube.psf).cuda(), **kw)
+    stream = torch.cuda.current_stream()
+
+    m.iterate(args.warmup)
+    torch.cuda.synchronize()
+    barrier()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with ClockSampler(local) as clk:
+        torch.cuda.synchronize()
+        e0.record(stream)
+        m.iterate(args.steps)
+        e1.record(stream)
+        torch.cuda.synchronize()
+    barrier()
+    ms = max_over_ranks(e0.elapsed_time(e1))
+    ms_step = ms / args.steps
+    value = voxels * world * args.steps / (ms / 1e3)
+    launches = m.kernels_per_iteration() * args.steps
+
+    # per-stage device times over a second timed region (events between stages on the launching stream)
+    names = [s for s in __import__("paper_1602_08847_gb300.muffin", fromlist=["stage_names"]).stage_names()]
+    stage_ms = m.iterate_timed(args.steps)
+    stage_bytes = m.stage_bytes()
+    k = int(np.argmax(stage_ms))
+    peaks = {}
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            peaks = json.load(f)
+    except OSError:
+        pass
+    peak = peaks.get("hbm_gbs", 6800.0)
+    peak_src = "measured" if "hbm_gbs" in peaks else "fallback"
+    ach = stage_bytes[k] * args.steps / (stage_ms[k] / 1e3) / 1e9
+    J = cfg.nscales
+    step_bytes = (8 * J + 30) * voxels
+    roofline = {"bound": "hbm", "kernel": names[k], "achieved": ach, "peak": peak, "unit": "GB/s",
+                "frac": ach / peak, "peak_source": peak_src, "traffic": None,
+                "stage_ms_per_step": {nm: t / args.steps for nm, t in zip(names, stage_ms)},
+                "stage_gbs": {nm: (b * args.steps / (t / 1e3) / 1e9 if t > 0 else 0.0)
+                              for nm, b, t in zip(names, stage_bytes, stage_ms)},
+                "step": {"algorithmic_bytes": step_bytes, "bytes_per_voxel": 8 * J + 30,
+                         "achieved": step_bytes / (ms_step / 1e3) / 1e9,
+                         "frac": step_bytes / (ms_step / 1e3) / 1e9 / peak}}
+    traffic_file = os.path.join(ROOT, "profiles", "traffic.json")
+    if os.path.exists(traffic_file):
+        with open(traffic_file) as f:
+            tr = json.load(f)
+        if tr.get("kernel") == names[k] and tr.get("workload") == args.config:
+            roofline["traffic"] = tr.get("bytes_per_launch")
+    m.close()
+    del m
+
+    line = {"metric": METRIC, "value": value, "unit": METRIC, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "voxels_per_gpu": voxels, "nscales": J, "iuwt_gen": 1,
+                       "l2": "inputs larger than L2 (state ~2.4 GB per cube)", "parallelism": f"replicas{world}",
+                       "graph": True},
+            "roofline": roofline, "gpu_launches": launches, "clocks": clk.summary()}
+
+    # end to end through the public call: pinned host cubes in, X back to host
+    if not args.no_e2e:
+        hd = torch.from_numpy(cube.dirty).pin_memory()
+        hp = torch.from_numpy(cube.psf).pin_memory()
+        solve(hd, hp, 1, **kw)          # warm the allocator and the kernels
+        torch.cuda.synchronize()
+        barrier()
+        t0 = time.perf_counter()
+        x = solve(hd, hp, args.steps, **kw)
+        torch.cuda.synchronize()
+        t = max_over_ranks(time.perf_counter() - t0)
+        line["e2e"] = {"value": voxels * world * args.steps / t, "unit": METRIC,
+                       "h2d_bytes_per_step": (hd.numel() + hp.numel()) * 4 / args.steps,
+                       "d2h_bytes_per_step": x.numel() * 4 / args.steps,
+                       "what": f"muffin.solve(): H2D of y and PSF, set-up (FP64 spectra, power method), "
+                               f"{args.steps} passes, D2H of X; one call"}
+
+    # plain method, time to 1e-4 relative objective on the 256x256x64 cube (F* from 2000 passes)
+    if not args.no_ttt and rank == 0:
+        cb = synth.make_cube("B")
+        mb = Muffin(torch.from_numpy(cb.dirty).cuda(), torch.from_numpy(cb.psf).cuda(), nscales=4, gen=1,
+                    mu_s=0.25, mu_l=3.0)
+        mb.iterate(2000)
+        fstar, _ = mb.objective()
+        mb.close()
+        mb = Muffin(torch.from_numpy(cb.dirty).cuda(), torch.from_numpy(cb.psf).cuda(), nscales=4, gen=1,
+                    mu_s=0.25, mu_l=3.0)
+        it, reached, chk = 0, None, 10
+        t_pass = 0.0
+        while it < 2000:
+            s0, s1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            s0.record()
+            mb.iterate(chk)
+            s1.record()
+            torch.cuda.synchronize()
+            t_pass += s0.elapsed_time(s1)
+            it += chk
+            f, _ = mb.objective()
+            if abs(f - fstar) / abs(fstar) <= 1e-4:
+                reached = it
+                break
+        mb.close()
+        line["time_to_rel_obj_1e-4"] = {"workload": "256x256x64, 40 sources, 60 antennas, J=4", "init": "zero",
+                                        "iterations": reached, "pass_ms_total": t_pass,
+                                        "f_star": fstar, "f_star_passes": 2000, "check_every": chk}
+
+    if rank == 0 and not args.no_cpu:
+        try:
+            res = oracle_time(args.config, 8, 3)
+            line["cpu_baseline"] = {"value": res["value"], "unit": METRIC, "cores": 1, "kind": "oracle",
+                                    "sample": f"{n}x{n}x8 slice of the workload, 3 passes, numpy FP64, 1 thread",
+                                    "seconds": res["seconds"]}
+        except Exception as exc:  # noqa: BLE001
+            line["cpu_baseline"] = {"value": None, "unit": METRIC, "cores": 1, "kind": "oracle",
+                                    "sample": "failed: " + str(exc)[:200]}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if dist:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

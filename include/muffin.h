@@ -1,0 +1,140 @@
+/*
+ * libmuffin -- GB300 (sm_103a) implementation of the primal-dual MUFFIN
+ * iteration (Deguignet, Ferrari, Mary, Ferrari, "Distributed multi-frequency
+ * image reconstruction for radio-interferometry", Sec. 3, Algorithm 1).
+ *
+ * Problem (Sec. 2, Eqs. 5-6), for a cube X = [x_1 .. x_L] of L channels of
+ * N x N pixels:
+ *     min_X  sum_l w_l/2 ||y_l - H_l x_l||^2 + 1_{R+}(X)
+ *            + mu_s sum_l ||W_s x_l||_1 + mu_lambda sum_n ||W_lambda x^n||_1
+ * with H_l the circular convolution by the PSF of channel l (Eq. 4), W_s the
+ * isotropic undecimated wavelet transform (B3 spline, J detail planes plus the
+ * coarse plane, periodic) and W_lambda the orthonormal DCT-II along channels.
+ *
+ * Conventions shared by every entry point:
+ *  - Cubes are float32, channel-major, row-major: element (l, y, x) of an
+ *    [L][N][N] cube is at l*N*N + y*N + x.  Wavelet coefficients U are
+ *    [L][J+1][N][N] (plane J is the coarse plane).
+ *  - Pointers named d_* are DEVICE pointers, h_* HOST pointers.  The library
+ *    never takes ownership of caller memory and never calls cudaMalloc: the
+ *    caller allocates the workspace (muffin_workspace_bytes) and every buffer.
+ *  - Work is enqueued on the stream given to muffin_init, asynchronously,
+ *    except calls that write host outputs (they synchronise that stream).
+ *  - Every call returns a muffin_status; on error, muffin_last_error() gives
+ *    a one-line description.  A failed call leaves the state it found unless
+ *    its description says otherwise.
+ *  - Call order: muffin_init -> muffin_set_psf -> muffin_iterate /
+ *    muffin_objective / ...; other orders return MUFFIN_ERR_STATE.
+ */
+#ifndef MUFFIN_H
+#define MUFFIN_H
+
+#include <stddef.h>
+#include <cuda_runtime_api.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct muffin_ctx muffin_ctx;
+
+typedef enum {
+  MUFFIN_OK = 0,
+  MUFFIN_ERR_ARG = -1,        /* bad size, pointer or parameter */
+  MUFFIN_ERR_CUDA = -2,       /* a CUDA call failed (message names it) */
+  MUFFIN_ERR_NOMEM = -3,      /* workspace too small */
+  MUFFIN_ERR_STATE = -4,      /* call out of order */
+  MUFFIN_ERR_NONFINITE = -5,  /* NaN or Inf in an input or in the state */
+  MUFFIN_ERR_TIMEOUT = -6     /* reserved: a bounded device wait gave up */
+} muffin_status;
+
+/* Parameters of Eqs. 5-6 and Algorithm 1. */
+typedef struct {
+  int nx, ny;            /* image size; nx == ny == N, N a power of two in [16, 1024] */
+  int nchan;             /* L >= 1; L <= 512 */
+  int nscales;           /* J >= 0 detail planes of W_s, 2^J < N */
+  int iuwt_gen;          /* 1: w_j = c_j - c_{j+1};  2: w_j = c_j - H_j c_{j+1} (Sec. 4) */
+  double mu_s;           /* spatial weight mu_s >= 0 (Eq. 6) */
+  double mu_l;           /* spectral weight mu_lambda >= 0 (Eq. 6) */
+  double tau;            /* primal step; <= 0: Condat's rule from power-iteration norms */
+  double sigma;          /* dual step; <= 0: 1 (Sec. 4 uses sigma = 1) */
+  double rho;            /* relaxation; <= 0: 1 */
+  const double* h_chan_weight; /* host, L weights w_l = 1/sigma_l^2 of Eq. 5; NULL: all 1 */
+  int fine_levels;       /* tiling split j1 of W_s (advanced); < 0: automatic */
+  int power_iters;       /* power-method passes for each operator norm; <= 0: 40 */
+} muffin_params;
+
+/* Bytes of device workspace a context with these parameters needs (0 if the
+ * parameters are invalid; see muffin_check_params). */
+size_t muffin_workspace_bytes(const muffin_params* p);
+
+/* MUFFIN_OK if the parameters describe a problem this library can solve,
+ * else MUFFIN_ERR_ARG with a reason in h_msg (may be NULL, >= 128 bytes). */
+int muffin_check_params(const muffin_params* p, char* h_msg, size_t msg_len);
+
+/* Create a context (Algorithm 1, "Initialize": X = U = V = 0).
+ * d_dirty: [L][N][N] dirty cube y of Eq. 4, copied into the workspace (the
+ * caller may free it afterwards).  d_workspace: caller-owned, at least
+ * muffin_workspace_bytes(p) bytes, 256-byte aligned, valid until
+ * muffin_destroy.  stream: where all work of this context is enqueued. */
+int muffin_init(muffin_ctx** ctx, const muffin_params* p, const float* d_dirty, void* d_workspace,
+                size_t ws_bytes, cudaStream_t stream);
+
+/* Set the PSFs (Eq. 4): d_psf [L][N][N], channel l's PSF with its peak at
+ * pixel (N/2, N/2).  Builds the Fourier multipliers of H_l^T H_l, the vector
+ * H_l^T y_l, the operator norms by the power method and, if tau was left to
+ * the library, the step sizes (Condat: 1/tau - sigma ||L||^2 > beta/2).
+ * Synchronises the stream. */
+int muffin_set_psf(muffin_ctx* ctx, const float* d_psf);
+
+/* Run n_iter >= 0 passes of Algorithm 1 (Eqs. 8-14), asynchronously. */
+int muffin_iterate(muffin_ctx* ctx, int n_iter);
+
+/* Objective of Eqs. 5-6 at the current X (positivity holds by construction):
+ * h_obj[0] = total; if h_terms != NULL it receives (data term, mu_s spatial
+ * l1, mu_lambda spectral l1).  FP64 FFT and FP64 reductions.  Synchronises. */
+int muffin_objective(muffin_ctx* ctx, double* h_obj, double* h_terms);
+
+/* Current X out to / in from a device cube [L][N][N] (warm start: set X and
+ * keep U, V). */
+int muffin_get_cube(muffin_ctx* ctx, float* d_x);
+int muffin_set_cube(muffin_ctx* ctx, const float* d_x);
+
+/* Full state (X [L][N][N], U [L][J+1][N][N], V [L][N][N], pass count) out /
+ * in, device buffers in the natural layout.  Restoring a saved state and
+ * iterating gives the same cube as never having stopped. */
+int muffin_get_state(muffin_ctx* ctx, float* d_x, float* d_u, float* d_v, long long* h_iter);
+int muffin_set_state(muffin_ctx* ctx, const float* d_x, const float* d_u, const float* d_v, long long iter);
+
+/* Change mu_s / mu_lambda (two-step calibration of Sec. 4: first mu_lambda
+ * = 0, then mu_lambda > 0 from the same X).  Automatic step sizes are
+ * recomputed; the state is kept. */
+int muffin_set_mu(muffin_ctx* ctx, double mu_s, double mu_l);
+
+/* Step sizes in use and the norms behind them: beta = max_l w_l ||H_l||^2 by
+ * the power method, l_norm2 = mu_s^2 ||W_s||^2 + mu_lambda^2, beta_closed =
+ * max_l w_l max_k |hhat_l(k)|^2 (exact, H_l is circulant).  Any pointer may
+ * be NULL. */
+int muffin_step_sizes(const muffin_ctx* ctx, double* tau, double* sigma, double* rho, double* beta,
+                      double* l_norm2, double* beta_closed, double* ws_norm2);
+
+/* Per-stage timing: run n_iter passes launching each kernel stage between
+ * CUDA events on the context stream (no graph); h_ms[k] receives the summed
+ * milliseconds of stage k for k < n_stages (see muffin_stage_name).
+ * Synchronises. */
+int muffin_iterate_timed(muffin_ctx* ctx, int n_iter, double* h_ms, int n_stages);
+int muffin_num_stages(void);
+const char* muffin_stage_name(int k);
+/* Bytes one launch of stage k must move at least (each input read once, each
+ * output written once) for this context; 0 if the stage does not run. */
+double muffin_stage_bytes(const muffin_ctx* ctx, int k);
+/* Number of kernels one pass of Algorithm 1 launches for this context. */
+int muffin_kernels_per_iteration(const muffin_ctx* ctx);
+
+const char* muffin_last_error(const muffin_ctx* ctx);  /* ctx may be NULL (init errors) */
+void muffin_destroy(muffin_ctx* ctx);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* MUFFIN_H */

@@ -1,0 +1,97 @@
+// Host-side launchers of the MUFFIN kernels (internal to libmuffin).
+#pragma once
+#include <cuda_runtime.h>
+#include <stddef.h>
+#include <stdint.h>
+
+namespace muffin {
+
+// Geometry of one cube as the kernels see it.
+struct Geom {
+  int n;        // image side N (power of two, 16..1024)
+  int L;        // channels
+  int J;        // IUWT detail scales
+  int gen;      // IUWT generation (1 or 2)
+  int j1;       // fine levels computed on halo tiles; levels >= j1 run class-permuted
+};
+
+// ---- FFT path (k_fft.cu) ----
+// Per-channel H_l^T H_l x_l (weights and 1/N^2 folded into Kp, Kb) followed
+// by the primal step of Algorithm 1, or, in power mode, only H^T H x -> out.
+cudaError_t launch_rows_fwd(const float* X, float* spec, int n, int L, const float* twf, cudaStream_t s);
+cudaError_t launch_cols_filter(float* spec, const float* Kp, const float* Kb, int n, int L, const float* twf,
+                               cudaStream_t s);
+struct PrimalArgs {
+  const float* b; const float* S; const float* T;
+  float* X; float* D;
+  float tau, mu_s, mu_l, rho;
+};
+cudaError_t launch_rows_inv_primal(const float* spec, const PrimalArgs& a, int n, int L, const float* twf,
+                                   cudaStream_t s);
+cudaError_t launch_rows_inv_plain(const float* spec, float* out, int n, int L, const float* twf, cudaStream_t s);
+
+// FP64 full-complex 2-D FFT helpers for setup and the objective.
+// mode_in: 0 complex input z; 1 real float input with ifftshift; 2 real float input.
+cudaError_t launch_c2c_rows64(const void* in, int mode_in, void* z, int n, int L, int dir, const void* twd,
+                              cudaStream_t s);
+cudaError_t launch_c2c_cols64(void* z, int n, int L, int dir, const void* twd, cudaStream_t s);
+cudaError_t launch_build_K(const void* hhat, const double* w, float* Kp, float* Kb, int n, int L, cudaStream_t s);
+cudaError_t launch_mul_conj(const void* hhat, void* z, int n, int L, cudaStream_t s);
+cudaError_t launch_real_to_float(const void* z, const double* w, float* out, int n, int L, cudaStream_t s);
+// sum_l w_l / (2 N^2) sum_k |hhat z - yhat|^2 over column tiles -> partials
+cudaError_t launch_cols64_fidelity(void* z, const void* hhat, const void* yhat, const double* w, int n, int L,
+                                   const void* twd, double* partials, int* nparts, cudaStream_t s);
+cudaError_t launch_max_abs2(const void* hhat, const double* w, int n, int L, double* partials, int* nparts,
+                            cudaStream_t s);
+
+// ---- IUWT (k_iuwt.cu) ----
+enum IuwtMode { MODE_UPDATE = 0, MODE_LINEAR = 1, MODE_NORM = 2, MODE_ADJ = 3 };
+struct IuwtArgs {
+  const float* D;    // analysis input (natural layout)
+  float* U;          // [L][J+1][N*N]; planes j >= j1 class-permuted (stride 2^j1)
+  float* cr;         // c_{j1} out of the fine analysis / r_{j1} out of the coarse part
+  const float* rin;  // r_{j1} read by the fine adjoint
+  float* S;          // W_s^T U out of the fine adjoint (natural)
+  float k;           // sigma * mu_s
+  float rho;
+  double* partials;  // NORM mode: one partial sum per block
+};
+size_t fine_smem_bytes(const Geom& g, int adjoint);
+size_t coarse_smem_bytes(const Geom& g);
+cudaError_t launch_fine_analysis(const Geom& g, const IuwtArgs& a, int mode, cudaStream_t s, int* nblocks);
+cudaError_t launch_fine_adjoint(const Geom& g, const IuwtArgs& a, cudaStream_t s);
+cudaError_t launch_coarse(const Geom& g, const float* c_in, float* r_out, float* U, float k, float rho, int mode,
+                          double* partials, cudaStream_t s, int* nblocks);
+cudaError_t iuwt_configure(const Geom& g);
+cudaError_t fft_configure(int n);
+
+// ---- spectral step (k_spectral.cu) ----
+enum SpecMode { SPEC_UPDATE = 0, SPEC_NORM = 1, SPEC_TONLY = 2 };
+struct SpecArgs {
+  const float* D;    // analysis input
+  float* V;          // dual variable (updated in place)
+  float* T;          // W_lambda^T V out (unscaled)
+  float k;           // sigma * mu_lambda
+  float rho;
+  const float* tw;   // FFT twiddles of length L (float2)
+  const float* post; // DCT post-twiddles (float2) [L]
+  const float* pre;  // inverse pre-twiddles (float2) [L]
+  const float* invs; // 1 / (s_k L) [L]
+  const float* dense;// dense orthonormal DCT matrix [L][L]
+  double* partials;
+};
+bool spectral_uses_fft(int L);
+cudaError_t spectral_configure(int L);
+cudaError_t launch_spectral(const SpecArgs& a, int npix, int L, int mode, cudaStream_t s, int* nblocks);
+
+// ---- misc (k_misc.cu) ----
+cudaError_t launch_sum_partials(const double* partials, int n, double* out, cudaStream_t s);
+cudaError_t launch_max_partials(const double* partials, int n, double* out, cudaStream_t s);
+cudaError_t launch_dot(const float* a, const float* b, size_t n, double* partials, int* nparts, cudaStream_t s);
+cudaError_t launch_scale(float* x, size_t n, const double* num, const double* den, cudaStream_t s);
+cudaError_t launch_fill_random(float* x, size_t n, uint64_t seed, cudaStream_t s);
+cudaError_t launch_permute_planes(const float* src, float* dst, int n, int L, int J, int j1, int to_class,
+                                  cudaStream_t s);
+cudaError_t launch_nonfinite_count(const float* x, size_t n, int* count, cudaStream_t s);
+
+}  // namespace muffin

@@ -1,0 +1,468 @@
+// FFT kernels of the data-fidelity gradient (Algorithm 1, first line; Eq. 8)
+// and of the FP64 setup / objective paths.
+//
+// Hot path, FP32, per channel l:  grad_l = F^-1(K_l . F x_l) - b_l with
+// K_l = w_l |hhat_l|^2 / N^2 (real, even) and b_l = w_l H_l^T y_l.
+//   k_rows_fwd      two real rows -> one complex FFT -> two half-spectrum rows.
+//                   The row spectrum is stored as N/2 complex numbers: bins
+//                   1..N/2-1, with bin 0 packed as (DC, Nyquist) (both real).
+//   k_cols_filter   column FFT, multiply by K, inverse column FFT, in place.
+//                   The packed column 0 carries the DC and Nyquist columns as
+//                   the real and imaginary parts of one complex sequence.
+//   k_rows_inv      inverse row FFT of two rows at once, then the primal
+//                   update of Algorithm 1 (second line; Eq. 10) in the
+//                   epilogue: X~ = (X - tau (grad + mu_s S + mu_l T))_+,
+//                   D = 2 X~ - X, X <- rho X~ + (1 - rho) X.
+#include "device.cuh"
+#include "internal.h"
+
+namespace muffin {
+
+template <int N> __host__ __device__ constexpr int rows_pairs() { return (2048 / N) < (N / 2) ? (2048 / N) : (N / 2); }
+template <int N> __host__ __device__ constexpr int cols_per_cta() { return N >= 1024 ? 8 : ((N / 2) < 16 ? (N / 2) : 16); }
+
+// ------------------------------------------------------------------ FP32 rows forward
+template <int N>
+__global__ void __launch_bounds__(rows_pairs<N>() * (N / 8))
+k_rows_fwd(const float* __restrict__ X, cpx<float>* __restrict__ spec, const cpx<float>* __restrict__ twg) {
+  constexpr int T8 = N / 8, PAIRS = rows_pairs<N>(), H = N / 2;
+  __shared__ cpx<float> tw[N];
+  __shared__ cpx<float> buf[PAIRS * N];
+  const int f = threadIdx.x / T8, t = threadIdx.x % T8;
+  for (int i = threadIdx.x; i < N; i += blockDim.x) tw[i] = twg[i];
+  const int l = blockIdx.y;
+  const int y0 = 2 * (blockIdx.x * PAIRS + f);
+  const float* r0 = X + ((size_t)l * N + y0) * N;
+  cpx<float> v[8];
+#pragma unroll
+  for (int q = 0; q < 8; ++q) v[q] = mk<float>(__ldg(r0 + t + q * T8), __ldg(r0 + N + t + q * T8));
+  __syncthreads();
+  fft_regs<float, N, -1, 1>(v, buf + f * N, tw, t);
+  __syncthreads();
+#pragma unroll
+  for (int q = 0; q < 8; ++q) buf[f * N + t + q * T8] = v[q];
+  __syncthreads();
+  cpx<float>* o0 = spec + ((size_t)l * N + y0) * H;
+  cpx<float>* o1 = o0 + H;
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    const int k = t + q * T8;
+    const cpx<float> zk = buf[f * N + k];
+    if (k == 0) {
+      const cpx<float> zn = buf[f * N + H];
+      o0[0] = mk<float>(zk.x, zn.x);
+      o1[0] = mk<float>(zk.y, zn.y);
+    } else {
+      const cpx<float> zm = buf[f * N + N - k];
+      o0[k] = mk<float>(0.5f * (zk.x + zm.x), 0.5f * (zk.y - zm.y));
+      o1[k] = mk<float>(0.5f * (zk.y + zm.y), 0.5f * (zm.x - zk.x));
+    }
+  }
+}
+
+// ------------------------------------------------------------------ FP32 column filter
+template <int N>
+__global__ void __launch_bounds__(cols_per_cta<N>() * (N / 8))
+k_cols_filter(cpx<float>* __restrict__ spec, const float* __restrict__ Kp, const float* __restrict__ Kb,
+              const cpx<float>* __restrict__ twg) {
+  constexpr int T8 = N / 8, C = cols_per_cta<N>(), H = N / 2;
+  extern __shared__ __align__(16) unsigned char smraw[];
+  cpx<float>* tw = reinterpret_cast<cpx<float>*>(smraw);
+  cpx<float>* buf = tw + N;
+  const int c = threadIdx.x % C, t = threadIdx.x / C;
+  for (int i = threadIdx.x; i < N; i += blockDim.x) tw[i] = twg[i];
+  const int l = blockIdx.y;
+  const int kx = blockIdx.x * C + c;
+  cpx<float>* base = spec + (size_t)l * N * H;
+  cpx<float> v[8];
+#pragma unroll
+  for (int q = 0; q < 8; ++q) v[q] = base[(t + q * T8) * H + kx];
+  __syncthreads();
+  fft_regs<float, N, -1, C>(v, buf + c, tw, t);
+  __syncthreads();
+#pragma unroll
+  for (int q = 0; q < 8; ++q) buf[(t + q * T8) * C + c] = v[q];
+  __syncthreads();
+  const float* Kl = Kp + (size_t)l * N * H;
+#pragma unroll
+  for (int q = 0; q < 8; ++q) {
+    const int pos = t + q * T8;
+    const float a = __ldg(Kl + pos * H + kx);
+    if (kx == 0) {
+      // (DC, Nyquist) packed column: Z'(k) = a Z(k) + b conj(Z(-k))
+      const cpx<float> zm = buf[((N - pos) & (N - 1)) * C + c];
+      const float bq = __ldg(Kb + (size_t)l * N + pos);
+      v[q] = add(scale(v[q], a), scale(conj(zm), bq));
+    } else {
+      v[q] = scale(v[q], a);
+    }
+  }
+  fft_regs<float, N, 1, C>(v, buf + c, tw, t);
+#pragma unroll
+  for (int q = 0; q < 8; ++q) base[(t + q * T8) * H + kx] = v[q];
+}
+
+// ------------------------------------------------------------------ FP32 rows inverse + primal
+template <int N, int MODE>
+__global__ void __launch_bounds__(rows_pairs<N>() * (N / 8))
+k_rows_inv(const cpx<float>* __restrict__ spec, PrimalArgs a, float* __restrict__ out,
+           const cpx<float>* __restrict__ twg) {
+  constexpr int T8 = N / 8, PAIRS = rows_pairs<N>(), H = N / 2;
+  __shared__ cpx<float> tw[N];
+  __shared__ cpx<float> buf[PAIRS * N];
+  const int f = threadIdx.x / T8, t = threadIdx.x % T8;
+  for (int i = threadIdx.x; i < N; i += blockDim.x) tw[i] = twg[i];
+  const int l = blockIdx.y;
+  const int y0 = 2 * (blockIdx.x * PAIRS + f);
+  const cpx<float>* s0 = spec + ((size_t)l * N + y0) * H;
+  const cpx<float>* s1 = s0 + H;
+  cpx<float> v[8];
+#pragma unroll
+  for (int q = 0; q < 8; ++q) {
+    const int pos = t + q * T8;
+    if (pos == 0) {
+      const cpx<float> A = s0[0], B = s1[0];
+      v[q] = mk<float>(A.x, B.x);
+    } else if (pos == H) {
+      const cpx<float> A = s0[0], B = s1[0];
+      v[q] = mk<float>(A.y, B.y);
+    } else if (pos < H) {
+      const cpx<float> A = s0[pos], B = s1[pos];
+      v[q] = mk<float>(A.x - B.y, A.y + B.x);
+    } else {
+      const cpx<float> A = s0[N - pos], B = s1[N - pos];
+      v[q] = mk<float>(A.x + B.y, B.x - A.y);
+    }
+  }
+  __syncthreads();
+  fft_regs<float, N, 1, 1>(v, buf + f * N, tw, t);
+  const size_t row0 = ((size_t)l * N + y0) * N;
+#pragma unroll
+  for (int q = 0; q < 8; ++q) {
+    const int x = t + q * T8;
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      const size_t idx = row0 + (size_t)h * N + x;
+      const float g = h == 0 ? v[q].x : v[q].y;
+      if (MODE == 0) {
+        float step = g - __ldg(a.b + idx);
+        if (a.S) step += a.mu_s * __ldg(a.S + idx);
+        if (a.T) step += a.mu_l * __ldg(a.T + idx);
+        const float xo = a.X[idx];
+        const float xt = fmaxf(xo - a.tau * step, 0.0f);
+        a.D[idx] = 2.0f * xt - xo;
+        a.X[idx] = a.rho * xt + (1.0f - a.rho) * xo;
+      } else {
+        out[idx] = g;
+      }
+    }
+  }
+}
+
+// ------------------------------------------------------------------ FP64 full complex FFT (setup, objective)
+template <int N> __host__ __device__ constexpr int rows64_per_cta() { return (2048 / N) < 1 ? 1 : (2048 / N); }
+
+template <int N, int DIR>
+__global__ void __launch_bounds__(rows64_per_cta<N>() * (N / 8))
+k_c2c_rows64(const void* __restrict__ in, int mode_in, cpx<double>* __restrict__ z, int nrows_total,
+             const cpx<double>* __restrict__ twg) {
+  constexpr int T8 = N / 8, R = rows64_per_cta<N>();
+  extern __shared__ __align__(16) unsigned char smraw[];
+  cpx<double>* tw = reinterpret_cast<cpx<double>*>(smraw);
+  cpx<double>* buf = tw + N;
+  const int f = threadIdx.x / T8, t = threadIdx.x % T8;
+  for (int i = threadIdx.x; i < N; i += blockDim.x) tw[i] = twg[i];
+  const int row = blockIdx.x * R + f;          // global row index l*N + y
+  const bool ok = row < nrows_total;
+  cpx<double> v[8];
+#pragma unroll
+  for (int q = 0; q < 8; ++q) {
+    const int x = t + q * T8;
+    v[q] = mk<double>(0.0, 0.0);
+    if (ok) {
+      if (mode_in == 0) {
+        v[q] = reinterpret_cast<const cpx<double>*>(in)[(size_t)row * N + x];
+      } else if (mode_in == 1) {
+        // PSF given with its peak at (N/2, N/2): read it moved to (0, 0)
+        const int l = row / N, y = row % N;
+        const float* p = reinterpret_cast<const float*>(in) + (size_t)l * N * N;
+        v[q] = mk<double>((double)p[((y + N / 2) & (N - 1)) * N + ((x + N / 2) & (N - 1))], 0.0);
+      } else {
+        v[q] = mk<double>((double)reinterpret_cast<const float*>(in)[(size_t)row * N + x], 0.0);
+      }
+    }
+  }
+  __syncthreads();
+  fft_regs<double, N, DIR, 1>(v, buf + f * N, tw, t);
+  if (ok) {
+#pragma unroll
+    for (int q = 0; q < 8; ++q) z[(size_t)row * N + t + q * T8] = v[q];
+  }
+}
+
+template <int N> __host__ __device__ constexpr int cols64_per_cta() { return N >= 512 ? 4 : 8; }
+
+// Column FFT of the full complex spectrum, in place.  With FID set (forward
+// only) the epilogue also sums w_l |hhat z - yhat|^2 / (2 N^2) of the block.
+template <int N, int DIR, int FID>
+__global__ void __launch_bounds__(cols64_per_cta<N>() * (N / 8))
+k_c2c_cols64(cpx<double>* __restrict__ z, const cpx<double>* __restrict__ twg, const cpx<double>* __restrict__ hhat,
+             const cpx<double>* __restrict__ yhat, const double* __restrict__ w, double* __restrict__ partials) {
+  constexpr int T8 = N / 8, C = cols64_per_cta<N>();
+  extern __shared__ __align__(16) unsigned char smraw[];
+  cpx<double>* tw = reinterpret_cast<cpx<double>*>(smraw);
+  cpx<double>* buf = tw + N;
+  __shared__ double red[32];
+  const int c = threadIdx.x % C, t = threadIdx.x / C;
+  for (int i = threadIdx.x; i < N; i += blockDim.x) tw[i] = twg[i];
+  const int l = blockIdx.y;
+  const int kx = blockIdx.x * C + c;
+  const size_t base = (size_t)l * N * N;
+  cpx<double> v[8];
+#pragma unroll
+  for (int q = 0; q < 8; ++q) v[q] = z[base + (size_t)(t + q * T8) * N + kx];
+  __syncthreads();
+  fft_regs<double, N, DIR, C>(v, buf + c, tw, t);
+  if (FID) {
+    double acc = 0.0;
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+      const size_t idx = base + (size_t)(t + q * T8) * N + kx;
+      const cpx<double> r = sub(mul(hhat[idx], v[q]), yhat[idx]);
+      acc += r.x * r.x + r.y * r.y;
+    }
+    const double tot = block_sum(acc, red);
+    if (threadIdx.x == 0)
+      partials[blockIdx.y * gridDim.x + blockIdx.x] = tot * w[l] * 0.5 / ((double)N * (double)N);
+  } else {
+#pragma unroll
+    for (int q = 0; q < 8; ++q) z[base + (size_t)(t + q * T8) * N + kx] = v[q];
+  }
+}
+
+__global__ void k_build_K(const cpx<double>* __restrict__ hhat, const double* __restrict__ w, float* __restrict__ Kp,
+                          float* __restrict__ Kb, int n, int L) {
+  const int H = n / 2;
+  const size_t total = (size_t)L * n * H;
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < total; i += (size_t)gridDim.x * blockDim.x) {
+    const int kx = (int)(i % H);
+    const size_t lr = i / H;              // l * n + ky
+    const int l = (int)(lr / n);
+    const double s = w[l] / ((double)n * (double)n);
+    const cpx<double> h0 = hhat[lr * n + kx];
+    const double k0 = h0.x * h0.x + h0.y * h0.y;
+    if (kx == 0) {
+      const cpx<double> hn = hhat[lr * n + H];
+      const double kn = hn.x * hn.x + hn.y * hn.y;
+      Kp[i] = (float)(0.5 * (k0 + kn) * s);
+      Kb[lr] = (float)(0.5 * (k0 - kn) * s);
+    } else {
+      Kp[i] = (float)(k0 * s);
+    }
+  }
+}
+
+__global__ void k_mul_conj(const cpx<double>* __restrict__ hhat, cpx<double>* __restrict__ z, size_t total) {
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < total; i += (size_t)gridDim.x * blockDim.x)
+    z[i] = mul(conj(hhat[i]), z[i]);
+}
+
+__global__ void k_real_to_float(const cpx<double>* __restrict__ z, const double* __restrict__ w, float* __restrict__ out,
+                                int n, size_t total) {
+  const double inv = 1.0 / ((double)n * (double)n);
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < total; i += (size_t)gridDim.x * blockDim.x) {
+    const int l = (int)(i / ((size_t)n * n));
+    out[i] = (float)(z[i].x * inv * w[l]);
+  }
+}
+
+__global__ void k_max_abs2(const cpx<double>* __restrict__ hhat, const double* __restrict__ w, int n, size_t total,
+                           double* __restrict__ partials) {
+  __shared__ double red[32];
+  double m = 0.0;
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < total; i += (size_t)gridDim.x * blockDim.x) {
+    const int l = (int)(i / ((size_t)n * n));
+    const cpx<double> h = hhat[i];
+    m = fmax(m, w[l] * (h.x * h.x + h.y * h.y));
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_down_sync(0xffffffffu, m, o));
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = m;
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    m = threadIdx.x < (blockDim.x + 31) / 32 ? red[threadIdx.x] : 0.0;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_down_sync(0xffffffffu, m, o));
+    if (threadIdx.x == 0) partials[blockIdx.x] = m;
+  }
+}
+
+// ------------------------------------------------------------------ launchers
+#define MUFFIN_N_SWITCH(n, CALL) \
+  switch (n) {                   \
+    case 16: CALL(16); break;    \
+    case 32: CALL(32); break;    \
+    case 64: CALL(64); break;    \
+    case 128: CALL(128); break;  \
+    case 256: CALL(256); break;  \
+    case 512: CALL(512); break;  \
+    case 1024: CALL(1024); break;\
+    default: return cudaErrorInvalidValue; \
+  }
+
+cudaError_t launch_rows_fwd(const float* X, float* spec, int n, int L, const float* twf, cudaStream_t s) {
+#define CALL(NN)                                                                                   \
+  {                                                                                                \
+    dim3 grid((NN / 2) / rows_pairs<NN>(), L);                                                     \
+    k_rows_fwd<NN><<<grid, rows_pairs<NN>() * (NN / 8), 0, s>>>(X, reinterpret_cast<cpx<float>*>(spec), \
+                                                               reinterpret_cast<const cpx<float>*>(twf)); \
+  }
+  MUFFIN_N_SWITCH(n, CALL)
+#undef CALL
+  return cudaGetLastError();
+}
+
+template <int N> static cudaError_t cols_filter_n(float* spec, const float* Kp, const float* Kb, int L, const float* twf,
+                                                  cudaStream_t s) {
+  constexpr int C = cols_per_cta<N>();
+  const size_t smem = (size_t)(N + N * C) * sizeof(cpx<float>);
+  dim3 grid((N / 2) / C, L);
+  k_cols_filter<N><<<grid, C * (N / 8), smem, s>>>(reinterpret_cast<cpx<float>*>(spec), Kp, Kb,
+                                                   reinterpret_cast<const cpx<float>*>(twf));
+  return cudaGetLastError();
+}
+
+cudaError_t launch_cols_filter(float* spec, const float* Kp, const float* Kb, int n, int L, const float* twf,
+                               cudaStream_t s) {
+#define CALL(NN) return cols_filter_n<NN>(spec, Kp, Kb, L, twf, s);
+  MUFFIN_N_SWITCH(n, CALL)
+#undef CALL
+  return cudaErrorInvalidValue;
+}
+
+cudaError_t launch_rows_inv_primal(const float* spec, const PrimalArgs& a, int n, int L, const float* twf,
+                                   cudaStream_t s) {
+#define CALL(NN)                                                                                            \
+  {                                                                                                         \
+    dim3 grid((NN / 2) / rows_pairs<NN>(), L);                                                              \
+    k_rows_inv<NN, 0><<<grid, rows_pairs<NN>() * (NN / 8), 0, s>>>(reinterpret_cast<const cpx<float>*>(spec), a, \
+                                                                   nullptr, reinterpret_cast<const cpx<float>*>(twf)); \
+  }
+  MUFFIN_N_SWITCH(n, CALL)
+#undef CALL
+  return cudaGetLastError();
+}
+
+cudaError_t launch_rows_inv_plain(const float* spec, float* out, int n, int L, const float* twf, cudaStream_t s) {
+  PrimalArgs a{};
+#define CALL(NN)                                                                                            \
+  {                                                                                                         \
+    dim3 grid((NN / 2) / rows_pairs<NN>(), L);                                                              \
+    k_rows_inv<NN, 1><<<grid, rows_pairs<NN>() * (NN / 8), 0, s>>>(reinterpret_cast<const cpx<float>*>(spec), a, \
+                                                                   out, reinterpret_cast<const cpx<float>*>(twf)); \
+  }
+  MUFFIN_N_SWITCH(n, CALL)
+#undef CALL
+  return cudaGetLastError();
+}
+
+template <int N, int DIR> static cudaError_t rows64_n(const void* in, int mode_in, void* z, int L, const void* twd,
+                                                      cudaStream_t s) {
+  constexpr int R = rows64_per_cta<N>();
+  const size_t smem = (size_t)(N + R * N) * sizeof(cpx<double>);
+  const int rows = L * N;
+  k_c2c_rows64<N, DIR><<<(rows + R - 1) / R, R * (N / 8), smem, s>>>(in, mode_in, reinterpret_cast<cpx<double>*>(z),
+                                                                     rows, reinterpret_cast<const cpx<double>*>(twd));
+  return cudaGetLastError();
+}
+
+cudaError_t launch_c2c_rows64(const void* in, int mode_in, void* z, int n, int L, int dir, const void* twd,
+                              cudaStream_t s) {
+#define CALL(NN) return dir < 0 ? rows64_n<NN, -1>(in, mode_in, z, L, twd, s) : rows64_n<NN, 1>(in, mode_in, z, L, twd, s);
+  MUFFIN_N_SWITCH(n, CALL)
+#undef CALL
+  return cudaErrorInvalidValue;
+}
+
+template <int N, int DIR, int FID>
+static cudaError_t cols64_n(void* z, int L, const void* twd, const void* hhat, const void* yhat, const double* w,
+                            double* partials, int* nparts, cudaStream_t s) {
+  constexpr int C = cols64_per_cta<N>();
+  const size_t smem = (size_t)(N + N * C) * sizeof(cpx<double>);
+  dim3 grid(N / C, L);
+  if (nparts) *nparts = grid.x * grid.y;
+  k_c2c_cols64<N, DIR, FID><<<grid, C * (N / 8), smem, s>>>(
+      reinterpret_cast<cpx<double>*>(z), reinterpret_cast<const cpx<double>*>(twd),
+      reinterpret_cast<const cpx<double>*>(hhat), reinterpret_cast<const cpx<double>*>(yhat), w, partials);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_c2c_cols64(void* z, int n, int L, int dir, const void* twd, cudaStream_t s) {
+#define CALL(NN)                                                                                     \
+  return dir < 0 ? cols64_n<NN, -1, 0>(z, L, twd, nullptr, nullptr, nullptr, nullptr, nullptr, s) \
+                 : cols64_n<NN, 1, 0>(z, L, twd, nullptr, nullptr, nullptr, nullptr, nullptr, s);
+  MUFFIN_N_SWITCH(n, CALL)
+#undef CALL
+  return cudaErrorInvalidValue;
+}
+
+cudaError_t launch_cols64_fidelity(void* z, const void* hhat, const void* yhat, const double* w, int n, int L,
+                                   const void* twd, double* partials, int* nparts, cudaStream_t s) {
+#define CALL(NN) return cols64_n<NN, -1, 1>(z, L, twd, hhat, yhat, w, partials, nparts, s);
+  MUFFIN_N_SWITCH(n, CALL)
+#undef CALL
+  return cudaErrorInvalidValue;
+}
+
+cudaError_t launch_build_K(const void* hhat, const double* w, float* Kp, float* Kb, int n, int L, cudaStream_t s) {
+  const size_t total = (size_t)L * n * (n / 2);
+  const int blocks = (int)((total + 255) / 256 < 65535 ? (total + 255) / 256 : 65535);
+  k_build_K<<<blocks, 256, 0, s>>>(reinterpret_cast<const cpx<double>*>(hhat), w, Kp, Kb, n, L);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_mul_conj(const void* hhat, void* z, int n, int L, cudaStream_t s) {
+  const size_t total = (size_t)L * n * n;
+  const int blocks = (int)((total + 255) / 256 < 65535 ? (total + 255) / 256 : 65535);
+  k_mul_conj<<<blocks, 256, 0, s>>>(reinterpret_cast<const cpx<double>*>(hhat), reinterpret_cast<cpx<double>*>(z),
+                                    total);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_real_to_float(const void* z, const double* w, float* out, int n, int L, cudaStream_t s) {
+  const size_t total = (size_t)L * n * n;
+  const int blocks = (int)((total + 255) / 256 < 65535 ? (total + 255) / 256 : 65535);
+  k_real_to_float<<<blocks, 256, 0, s>>>(reinterpret_cast<const cpx<double>*>(z), w, out, n, total);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_max_abs2(const void* hhat, const double* w, int n, int L, double* partials, int* nparts,
+                            cudaStream_t s) {
+  const size_t total = (size_t)L * n * n;
+  int blocks = (int)((total + 255) / 256);
+  if (blocks > 1024) blocks = 1024;
+  *nparts = blocks;
+  k_max_abs2<<<blocks, 256, 0, s>>>(reinterpret_cast<const cpx<double>*>(hhat), w, n, total, partials);
+  return cudaGetLastError();
+}
+
+// Shared-memory opt-in of the instantiations for side n.  Called once per
+// context before any launch (and so before any stream capture).
+template <int N> static cudaError_t configure_n() {
+  cudaError_t e;
+  if ((e = allow_max_dyn_smem(k_cols_filter<N>))) return e;
+  if ((e = allow_max_dyn_smem(k_c2c_rows64<N, -1>))) return e;
+  if ((e = allow_max_dyn_smem(k_c2c_rows64<N, 1>))) return e;
+  if ((e = allow_max_dyn_smem(k_c2c_cols64<N, -1, 0>))) return e;
+  if ((e = allow_max_dyn_smem(k_c2c_cols64<N, 1, 0>))) return e;
+  return allow_max_dyn_smem(k_c2c_cols64<N, -1, 1>);
+}
+
+cudaError_t fft_configure(int n) {
+#define CALL(NN) return configure_n<NN>();
+  MUFFIN_N_SWITCH(n, CALL)
+#undef CALL
+  return cudaErrorInvalidValue;
+}
+
+}  // namespace muffin

@@ -1,0 +1,677 @@
+// Host runtime of libmuffin: parameter checks, workspace layout, set-up
+// (Fourier multipliers, H^T y, operator norms, step sizes), the per-pass
+// kernel sequence of Algorithm 1 captured once in a CUDA graph, the FP64
+// objective, state save / restore and per-stage timing.
+#include "muffin.h"
+#include "internal.h"
+
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+using namespace muffin;
+
+namespace {
+
+thread_local std::string g_init_error;
+constexpr int kMaxSmem = 232448;   // dynamic shared memory a block may opt into on sm_100/sm_103
+constexpr int kNumStages = 7;
+const char* kStageNames[kNumStages] = {"iuwt_fine_adjoint", "fft_rows_fwd", "fft_cols_filter", "fft_rows_inv_primal",
+                                       "iuwt_fine_analysis", "iuwt_coarse", "spectral_dct"};
+
+bool is_pow2(int v) { return v > 0 && (v & (v - 1)) == 0; }
+int ilog2(int v) { int r = 0; while ((1 << r) < v) ++r; return r; }
+
+size_t coarse_bytes(int n, int gen, int j1) {
+  const size_t M = (size_t)(n >> j1);
+  return (gen == 1 ? 2 : 3) * M * M * sizeof(float);
+}
+
+// Smallest split j1 whose coarse sub-images fit in shared memory.
+int auto_j1(int n, int J, int gen) {
+  if (J == 0) return 0;
+  const int top = J < 3 ? J : 3;
+  for (int j1 = 0; j1 <= top; ++j1) {
+    if (j1 > 0 && n < 64) break;
+    if (J == j1 || coarse_bytes(n, gen, j1) <= 200 * 1024) return j1;
+  }
+  return -1;
+}
+
+int check(const muffin_params* p, std::string* why) {
+  auto fail = [&](const char* m) { if (why) *why = m; return (int)MUFFIN_ERR_ARG; };
+  if (!p) return fail("params is NULL");
+  if (p->nx != p->ny) return fail("nx != ny: only square images are supported");
+  if (!is_pow2(p->nx) || p->nx < 16 || p->nx > 1024) return fail("N must be a power of two in [16, 1024]");
+  if (p->nchan < 1 || p->nchan > 512) return fail("nchan must be in [1, 512]");
+  if (p->nscales < 0 || (1 << p->nscales) >= p->nx) return fail("nscales J must satisfy 0 <= J and 2^J < N");
+  if (p->iuwt_gen != 1 && p->iuwt_gen != 2) return fail("iuwt_gen must be 1 or 2");
+  if (!(p->mu_s >= 0.0) || !std::isfinite(p->mu_s) || !(p->mu_l >= 0.0) || !std::isfinite(p->mu_l))
+    return fail("mu_s and mu_l must be finite and >= 0");
+  if (!std::isfinite(p->tau) || !std::isfinite(p->sigma) || !std::isfinite(p->rho)) return fail("non-finite step size");
+  if (p->rho >= 2.0) return fail("rho must be < 2");
+  if (p->h_chan_weight) {
+    for (int l = 0; l < p->nchan; ++l)
+      if (!(p->h_chan_weight[l] > 0.0) || !std::isfinite(p->h_chan_weight[l])) return fail("channel weights must be finite and > 0");
+  }
+  int j1 = p->fine_levels;
+  if (j1 < 0) {
+    j1 = auto_j1(p->nx, p->nscales, p->iuwt_gen);
+    if (j1 < 0) return fail("no wavelet tiling fits shared memory");
+  } else {
+    const int top = p->nscales < 3 ? p->nscales : 3;
+    if (j1 > top) return fail("fine_levels must be <= min(J, 3)");
+    if (j1 > 0 && p->nx < 64) return fail("fine_levels > 0 needs N >= 64");
+    if (p->nscales > j1 && coarse_bytes(p->nx, p->iuwt_gen, j1) > (size_t)kMaxSmem)
+      return fail("fine_levels too small: coarse sub-image does not fit shared memory");
+  }
+  return MUFFIN_OK;
+}
+
+struct Layout {
+  size_t X, U, V, y, b, Kp, Kb, spec, S, T, D, cr, hhat, yhat, z64, pw, partials, scal;
+  size_t twf, twd, twL, post, pre, invs, dense, w;
+  size_t total;
+  int max_parts;
+  int j1;
+};
+
+Layout make_layout(const muffin_params* p) {
+  Layout Lo{};
+  const size_t n = p->nx, L = p->nchan, J = p->nscales, P = n * n;
+  Lo.j1 = p->fine_levels >= 0 ? p->fine_levels : auto_j1(p->nx, p->nscales, p->iuwt_gen);
+  size_t off = 0;
+  auto take = [&](size_t bytes) { off = (off + 255) & ~(size_t)255; const size_t o = off; off += bytes; return o; };
+  Lo.X = take(L * P * 4);
+  Lo.U = take(L * (J + 1) * P * 4);
+  Lo.V = take(L * P * 4);
+  Lo.y = take(L * P * 4);
+  Lo.b = take(L * P * 4);
+  Lo.Kp = take(L * n * (n / 2) * 4);
+  Lo.Kb = take(L * n * 4);
+  Lo.spec = take(L * P * 4);
+  Lo.S = take(L * P * 4);
+  Lo.T = take(L * P * 4);
+  Lo.D = take(L * P * 4);
+  Lo.cr = take(L * P * 4);
+  Lo.hhat = take(L * P * 16);
+  Lo.yhat = take(L * P * 16);
+  Lo.z64 = take(L * P * 16);
+  Lo.pw = take((J + 4) * P * 4);
+  size_t mp = 1024;
+  mp = std::max(mp, (n / 64) * (n / 64) * L);
+  mp = std::max(mp, ((size_t)1 << (2 * Lo.j1)) * L);
+  mp = std::max(mp, (P + 31) / 32);
+  mp = std::max(mp, (n / 4) * L);
+  mp = std::max(mp, (size_t)4096);
+  Lo.max_parts = (int)mp;
+  Lo.partials = take(mp * 8);
+  Lo.scal = take(64 * 8);
+  Lo.twf = take(n * 8);
+  Lo.twd = take(n * 16);
+  Lo.twL = take(L * 8);
+  Lo.post = take(L * 8);
+  Lo.pre = take(L * 8);
+  Lo.invs = take(L * 4);
+  Lo.dense = take(L * L * 4);
+  Lo.w = take(L * 8);
+  Lo.total = (off + 255) & ~(size_t)255;
+  return Lo;
+}
+
+}  // namespace
+
+struct muffin_ctx {
+  muffin_params p;
+  Geom g;
+  Layout lo;
+  cudaStream_t stream = nullptr;
+  cudaStream_t cap = nullptr;
+  char* ws = nullptr;
+  std::vector<double> w;
+  int state = 0;          // 0 initialised, 1 PSF set
+  long long iter = 0;
+  double mu_s, mu_l, tau, sigma, rho;
+  double beta = 0, beta_closed = 0, ws_norm2 = 1, l_norm2 = 0;
+  bool tau_auto = true;
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  std::string err;
+
+  template <typename T> T* at(size_t off) const { return reinterpret_cast<T*>(ws + off); }
+  float* X() const { return at<float>(lo.X); }
+  float* U() const { return at<float>(lo.U); }
+  float* V() const { return at<float>(lo.V); }
+  size_t P() const { return (size_t)g.n * g.n; }
+  size_t vox() const { return (size_t)g.L * P(); }
+  double* partials() const { return at<double>(lo.partials); }
+  double* scal() const { return at<double>(lo.scal); }
+  // W_s^T U as the primal step reads it
+  const float* S_ptr() const { return g.J == 0 ? U() : at<float>(lo.S); }
+};
+
+#define CK(call)                                                                       \
+  do {                                                                                 \
+    cudaError_t e_ = (call);                                                           \
+    if (e_ != cudaSuccess) return fail(ctx, MUFFIN_ERR_CUDA, #call, cudaGetErrorString(e_)); \
+  } while (0)
+
+static int fail(muffin_ctx* ctx, int code, const char* what, const char* detail = nullptr) {
+  std::string m = what;
+  if (detail) { m += ": "; m += detail; }
+  if (ctx) ctx->err = m; else g_init_error = m;
+  return code;
+}
+
+static void drop_graph(muffin_ctx* ctx) {
+  if (ctx->exec) cudaGraphExecDestroy(ctx->exec);
+  if (ctx->graph) cudaGraphDestroy(ctx->graph);
+  ctx->exec = nullptr;
+  ctx->graph = nullptr;
+}
+
+static void compute_steps(muffin_ctx* ctx) {
+  ctx->l_norm2 = ctx->mu_s * ctx->mu_s * ctx->ws_norm2 + ctx->mu_l * ctx->mu_l;
+  if (ctx->tau_auto) ctx->tau = 0.99 / (0.5 * ctx->beta + ctx->sigma * ctx->l_norm2);
+}
+
+// ----------------------------------------------------------------- one pass of Algorithm 1
+struct StageTimer {
+  std::vector<cudaEvent_t>* ev;
+  std::vector<int>* stage;
+  cudaStream_t s;
+  void mark(int k) {
+    cudaEvent_t e;
+    cudaEventCreate(&e);
+    cudaEventRecord(e, s);
+    ev->push_back(e);
+    stage->push_back(k);
+  }
+};
+
+static int enqueue_pass(muffin_ctx* ctx, cudaStream_t s, StageTimer* tm) {
+  const Geom& g = ctx->g;
+  const Layout& lo = ctx->lo;
+  const bool spatial = ctx->mu_s != 0.0, spectral = ctx->mu_l != 0.0;
+  IuwtArgs ia{};
+  ia.D = ctx->at<float>(lo.D);
+  ia.U = ctx->U();
+  ia.cr = ctx->at<float>(lo.cr);
+  ia.rin = ctx->at<float>(lo.cr);
+  ia.S = ctx->at<float>(lo.S);
+  ia.k = (float)(ctx->sigma * ctx->mu_s);
+  ia.rho = (float)ctx->rho;
+  auto mark = [&](int k) { if (tm) tm->mark(k); };
+  mark(-1);
+  if (spatial && g.J > 0 && g.j1 > 0) {
+    CK(launch_fine_adjoint(g, ia, s));
+    mark(0);
+  }
+  CK(launch_rows_fwd(ctx->X(), ctx->at<float>(lo.spec), g.n, g.L, ctx->at<float>(lo.twf), s));
+  mark(1);
+  CK(launch_cols_filter(ctx->at<float>(lo.spec), ctx->at<float>(lo.Kp), ctx->at<float>(lo.Kb), g.n, g.L,
+                        ctx->at<float>(lo.twf), s));
+  mark(2);
+  PrimalArgs pa{};
+  pa.b = ctx->at<float>(lo.b);
+  pa.S = spatial ? ctx->S_ptr() : nullptr;
+  pa.T = spectral ? ctx->at<float>(lo.T) : nullptr;
+  pa.X = ctx->X();
+  pa.D = ctx->at<float>(lo.D);
+  pa.tau = (float)ctx->tau;
+  pa.mu_s = (float)ctx->mu_s;
+  pa.mu_l = (float)ctx->mu_l;
+  pa.rho = (float)ctx->rho;
+  CK(launch_rows_inv_primal(ctx->at<float>(lo.spec), pa, g.n, g.L, ctx->at<float>(lo.twf), s));
+  mark(3);
+  if (spatial) {
+    if (g.j1 > 0 || g.J == 0) {
+      CK(launch_fine_analysis(g, ia, MODE_UPDATE, s, nullptr));
+      mark(4);
+    }
+    if (g.J > g.j1) {
+      const float* cin = g.j1 > 0 ? ctx->at<float>(lo.cr) : ctx->at<float>(lo.D);
+      float* rout = g.j1 > 0 ? ctx->at<float>(lo.cr) : ctx->at<float>(lo.S);
+      CK(launch_coarse(g, cin, rout, ctx->U(), ia.k, ia.rho, MODE_UPDATE, nullptr, s, nullptr));
+      mark(5);
+    }
+  }
+  if (spectral) {
+    SpecArgs sa{};
+    sa.D = ctx->at<float>(lo.D);
+    sa.V = ctx->V();
+    sa.T = ctx->at<float>(lo.T);
+    sa.k = (float)(ctx->sigma * ctx->mu_l);
+    sa.rho = (float)ctx->rho;
+    sa.tw = ctx->at<float>(lo.twL);
+    sa.post = ctx->at<float>(lo.post);
+    sa.pre = ctx->at<float>(lo.pre);
+    sa.invs = ctx->at<float>(lo.invs);
+    sa.dense = ctx->at<float>(lo.dense);
+    CK(launch_spectral(sa, (int)ctx->P(), g.L, SPEC_UPDATE, s, nullptr));
+    mark(6);
+  }
+  return MUFFIN_OK;
+}
+
+// T = W_lambda^T V and r_{j1} of W_s^T U from the stored duals (after a state load).
+static int refresh_adjoints(muffin_ctx* ctx) {
+  const Geom& g = ctx->g;
+  const Layout& lo = ctx->lo;
+  SpecArgs sa{};
+  sa.D = ctx->at<float>(lo.D);
+  sa.V = ctx->V();
+  sa.T = ctx->at<float>(lo.T);
+  sa.tw = ctx->at<float>(lo.twL);
+  sa.post = ctx->at<float>(lo.post);
+  sa.pre = ctx->at<float>(lo.pre);
+  sa.invs = ctx->at<float>(lo.invs);
+  sa.dense = ctx->at<float>(lo.dense);
+  sa.rho = 1.0f;
+  CK(launch_spectral(sa, (int)ctx->P(), g.L, SPEC_TONLY, ctx->stream, nullptr));
+  if (g.J > g.j1) {
+    float* rout = g.j1 > 0 ? ctx->at<float>(lo.cr) : ctx->at<float>(lo.S);
+    CK(launch_coarse(g, nullptr, rout, ctx->U(), 0.f, 1.f, MODE_ADJ, nullptr, ctx->stream, nullptr));
+  }
+  return MUFFIN_OK;
+}
+
+static void host_tables(const muffin_ctx* ctx, std::vector<char>& blob, const Layout& lo, size_t base) {
+  const int n = ctx->g.n, L = ctx->g.L;
+  auto put = [&](size_t off, const void* src, size_t bytes) { std::memcpy(blob.data() + (off - base), src, bytes); };
+  const double pi = 3.14159265358979323846;
+  std::vector<float> twf(2 * n);
+  std::vector<double> twd(2 * n);
+  for (int m = 0; m < n; ++m) {
+    const double a = -2.0 * pi * m / n;
+    twd[2 * m] = std::cos(a); twd[2 * m + 1] = std::sin(a);
+    twf[2 * m] = (float)twd[2 * m]; twf[2 * m + 1] = (float)twd[2 * m + 1];
+  }
+  put(lo.twf, twf.data(), twf.size() * 4);
+  put(lo.twd, twd.data(), twd.size() * 8);
+  std::vector<float> twL(2 * L), post(2 * L), pre(2 * L), invs(L), dense((size_t)L * L);
+  for (int k = 0; k < L; ++k) {
+    const double a = -2.0 * pi * k / L;
+    twL[2 * k] = (float)std::cos(a); twL[2 * k + 1] = (float)std::sin(a);
+    const double sk = k == 0 ? std::sqrt(1.0 / L) : std::sqrt(2.0 / L);
+    const double b = pi * k / (2.0 * L);
+    post[2 * k] = (float)(sk * std::cos(-b)); post[2 * k + 1] = (float)(sk * std::sin(-b));
+    pre[2 * k] = (float)std::cos(b); pre[2 * k + 1] = (float)std::sin(b);
+    invs[k] = (float)(1.0 / (sk * L));
+    for (int l = 0; l < L; ++l) dense[(size_t)k * L + l] = (float)(sk * std::cos(pi * (2 * l + 1) * k / (2.0 * L)));
+  }
+  put(lo.twL, twL.data(), twL.size() * 4);
+  put(lo.post, post.data(), post.size() * 4);
+  put(lo.pre, pre.data(), pre.size() * 4);
+  put(lo.invs, invs.data(), invs.size() * 4);
+  put(lo.dense, dense.data(), dense.size() * 4);
+  put(lo.w, ctx->w.data(), ctx->w.size() * 8);
+}
+
+// ----------------------------------------------------------------- C ABI
+extern "C" {
+
+size_t muffin_workspace_bytes(const muffin_params* p) {
+  if (check(p, nullptr) != MUFFIN_OK) return 0;
+  return make_layout(p).total;
+}
+
+int muffin_check_params(const muffin_params* p, char* h_msg, size_t msg_len) {
+  std::string why;
+  const int r = check(p, &why);
+  if (h_msg && msg_len) {
+    std::snprintf(h_msg, msg_len, "%s", r == MUFFIN_OK ? "ok" : why.c_str());
+  }
+  return r;
+}
+
+int muffin_init(muffin_ctx** out, const muffin_params* p, const float* d_dirty, void* d_workspace, size_t ws_bytes,
+                cudaStream_t stream) {
+  muffin_ctx* ctx = nullptr;
+  if (!out) return fail(nullptr, MUFFIN_ERR_ARG, "ctx out-pointer is NULL");
+  *out = nullptr;
+  std::string why;
+  if (check(p, &why) != MUFFIN_OK) return fail(nullptr, MUFFIN_ERR_ARG, why.c_str());
+  if (!d_dirty || !d_workspace) return fail(nullptr, MUFFIN_ERR_ARG, "NULL dirty cube or workspace");
+  if (((uintptr_t)d_workspace & 255) != 0) return fail(nullptr, MUFFIN_ERR_ARG, "workspace must be 256-byte aligned");
+  const Layout lo = make_layout(p);
+  if (ws_bytes < lo.total) return fail(nullptr, MUFFIN_ERR_NOMEM, "workspace smaller than muffin_workspace_bytes()");
+  ctx = new muffin_ctx();
+  ctx->p = *p;
+  ctx->p.h_chan_weight = nullptr;
+  ctx->lo = lo;
+  ctx->g = Geom{p->nx, p->nchan, p->nscales, p->iuwt_gen, lo.j1};
+  ctx->stream = stream;
+  ctx->ws = reinterpret_cast<char*>(d_workspace);
+  ctx->w.assign(p->nchan, 1.0);
+  if (p->h_chan_weight) for (int l = 0; l < p->nchan; ++l) ctx->w[l] = p->h_chan_weight[l];
+  ctx->mu_s = p->mu_s;
+  ctx->mu_l = p->mu_l;
+  ctx->sigma = p->sigma > 0 ? p->sigma : 1.0;
+  ctx->rho = p->rho > 0 ? p->rho : 1.0;
+  ctx->tau_auto = !(p->tau > 0);
+  ctx->tau = p->tau > 0 ? p->tau : 0.0;
+  if (ctx->p.power_iters <= 0) ctx->p.power_iters = 40;
+  auto bail = [&](int code) { if (ctx->cap) cudaStreamDestroy(ctx->cap); g_init_error = ctx->err; delete ctx; return code; };
+  cudaError_t e;
+  if ((e = cudaStreamCreateWithFlags(&ctx->cap, cudaStreamNonBlocking))) { fail(ctx, MUFFIN_ERR_CUDA, "cudaStreamCreate", cudaGetErrorString(e)); return bail(MUFFIN_ERR_CUDA); }
+  if ((e = fft_configure(ctx->g.n)) || (e = iuwt_configure(ctx->g)) || (e = spectral_configure(ctx->g.L))) {
+    fail(ctx, MUFFIN_ERR_CUDA, "kernel configuration", cudaGetErrorString(e));
+    return bail(MUFFIN_ERR_CUDA);
+  }
+  // zero everything (X = U = V = 0 and every derived buffer), then the dirty cube and the tables
+  if ((e = cudaMemsetAsync(ctx->ws, 0, lo.total, stream))) { fail(ctx, MUFFIN_ERR_CUDA, "cudaMemsetAsync", cudaGetErrorString(e)); return bail(MUFFIN_ERR_CUDA); }
+  if ((e = cudaMemcpyAsync(ctx->at<float>(lo.y), d_dirty, ctx->vox() * 4, cudaMemcpyDeviceToDevice, stream))) {
+    fail(ctx, MUFFIN_ERR_CUDA, "copy of the dirty cube", cudaGetErrorString(e));
+    return bail(MUFFIN_ERR_CUDA);
+  }
+  const size_t tbase = lo.twf, tend = lo.w + ctx->w.size() * 8;
+  std::vector<char> blob(tend - tbase, 0);
+  host_tables(ctx, blob, lo, tbase);
+  if ((e = cudaMemcpyAsync(ctx->ws + tbase, blob.data(), blob.size(), cudaMemcpyHostToDevice, stream))) {
+    fail(ctx, MUFFIN_ERR_CUDA, "table upload", cudaGetErrorString(e));
+    return bail(MUFFIN_ERR_CUDA);
+  }
+  int* cnt = reinterpret_cast<int*>(ctx->scal() + 63);
+  int h_cnt = 0;
+  if ((e = launch_nonfinite_count(ctx->at<float>(lo.y), ctx->vox(), cnt, stream)) ||
+      (e = cudaMemcpyAsync(&h_cnt, cnt, sizeof(int), cudaMemcpyDeviceToHost, stream)) || (e = cudaStreamSynchronize(stream))) {
+    fail(ctx, MUFFIN_ERR_CUDA, "init", cudaGetErrorString(e));
+    return bail(MUFFIN_ERR_CUDA);
+  }
+  if (h_cnt) { fail(ctx, MUFFIN_ERR_NONFINITE, "dirty cube holds NaN or Inf"); return bail(MUFFIN_ERR_NONFINITE); }
+  *out = ctx;
+  return MUFFIN_OK;
+}
+
+int muffin_set_psf(muffin_ctx* ctx, const float* d_psf) {
+  if (!ctx) return fail(nullptr, MUFFIN_ERR_ARG, "ctx is NULL");
+  if (!d_psf) return fail(ctx, MUFFIN_ERR_ARG, "psf is NULL");
+  const Geom& g = ctx->g;
+  const Layout& lo = ctx->lo;
+  cudaStream_t s = ctx->stream;
+  const int n = g.n, L = g.L;
+  const size_t P = ctx->P(), V = ctx->vox();
+  double* sc = ctx->scal();
+  int* cnt = reinterpret_cast<int*>(sc + 63);
+  int h_cnt = 0;
+  CK(cudaMemsetAsync(cnt, 0, sizeof(int), s));
+  CK(launch_nonfinite_count(d_psf, V, cnt, s));
+  CK(cudaMemcpyAsync(&h_cnt, cnt, sizeof(int), cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  if (h_cnt) return fail(ctx, MUFFIN_ERR_NONFINITE, "psf holds NaN or Inf");
+  void* hh = ctx->ws + lo.hhat;
+  void* yh = ctx->ws + lo.yhat;
+  void* z = ctx->ws + lo.z64;
+  const void* twd = ctx->ws + lo.twd;
+  const double* w = ctx->at<double>(lo.w);
+  // hhat_l = DFT of the PSF moved to the origin; yhat_l = DFT of y_l (FP64)
+  CK(launch_c2c_rows64(d_psf, 1, hh, n, L, -1, twd, s));
+  CK(launch_c2c_cols64(hh, n, L, -1, twd, s));
+  CK(launch_c2c_rows64(ctx->at<float>(lo.y), 2, yh, n, L, -1, twd, s));
+  CK(launch_c2c_cols64(yh, n, L, -1, twd, s));
+  CK(launch_build_K(hh, w, ctx->at<float>(lo.Kp), ctx->at<float>(lo.Kb), n, L, s));
+  // b_l = w_l H_l^T y_l = w_l IDFT(conj(hhat) yhat)
+  CK(cudaMemcpyAsync(z, yh, V * 16, cudaMemcpyDeviceToDevice, s));
+  CK(launch_mul_conj(hh, z, n, L, s));
+  CK(launch_c2c_cols64(z, n, L, 1, twd, s));
+  CK(launch_c2c_rows64(z, 0, z, n, L, 1, twd, s));
+  CK(launch_real_to_float(z, w, ctx->at<float>(lo.b), n, L, s));
+  int np = 0;
+  CK(launch_max_abs2(hh, w, n, L, ctx->partials(), &np, s));
+  CK(launch_max_partials(ctx->partials(), np, sc + 0, s));
+  // beta: power method on the block-diagonal H^T H (K already holds w_l / N^2)
+  float* pv = reinterpret_cast<float*>(z);
+  float* pw = pv + V;
+  float* spec = ctx->at<float>(lo.spec);
+  const float* twf = ctx->at<float>(lo.twf);
+  CK(launch_fill_random(pv, V, 0x5eedULL, s));
+  CK(launch_dot(pv, pv, V, ctx->partials(), &np, s));
+  CK(launch_sum_partials(ctx->partials(), np, sc + 1, s));
+  CK(launch_scale(pv, V, nullptr, sc + 1, s));
+  for (int it = 0; it < ctx->p.power_iters; ++it) {
+    CK(launch_rows_fwd(pv, spec, n, L, twf, s));
+    CK(launch_cols_filter(spec, ctx->at<float>(lo.Kp), ctx->at<float>(lo.Kb), n, L, twf, s));
+    CK(launch_rows_inv_plain(spec, pw, n, L, twf, s));
+    CK(launch_dot(pv, pw, V, ctx->partials(), &np, s));
+    CK(launch_sum_partials(ctx->partials(), np, sc + 2, s));
+    CK(launch_dot(pw, pw, V, ctx->partials(), &np, s));
+    CK(launch_sum_partials(ctx->partials(), np, sc + 1, s));
+    CK(launch_scale(pw, V, nullptr, sc + 1, s));
+    std::swap(pv, pw);
+  }
+  // ||W_s||^2: power method on W_s^T W_s over one N x N plane
+  if (g.J > 0) {
+    Geom g1 = g;
+    g1.L = 1;
+    float* x = ctx->at<float>(lo.pw);
+    float* Ut = x + P;
+    float* crt = Ut + (size_t)(g.J + 1) * P;
+    float* St = crt + P;
+    IuwtArgs ia{};
+    ia.D = x; ia.U = Ut; ia.cr = crt; ia.rin = crt; ia.S = St; ia.k = 1.f; ia.rho = 1.f;
+    CK(launch_fill_random(x, P, 0x5eed2ULL, s));
+    CK(launch_dot(x, x, P, ctx->partials(), &np, s));
+    CK(launch_sum_partials(ctx->partials(), np, sc + 4, s));
+    CK(launch_scale(x, P, nullptr, sc + 4, s));
+    for (int it = 0; it < ctx->p.power_iters; ++it) {
+      if (g1.j1 > 0) CK(launch_fine_analysis(g1, ia, MODE_LINEAR, s, nullptr));
+      if (g1.J > g1.j1)
+        CK(launch_coarse(g1, g1.j1 > 0 ? crt : x, g1.j1 > 0 ? crt : St, Ut, 1.f, 1.f, MODE_LINEAR, nullptr, s, nullptr));
+      if (g1.j1 > 0) CK(launch_fine_adjoint(g1, ia, s));
+      CK(launch_dot(x, St, P, ctx->partials(), &np, s));
+      CK(launch_sum_partials(ctx->partials(), np, sc + 3, s));
+      CK(launch_dot(St, St, P, ctx->partials(), &np, s));
+      CK(launch_sum_partials(ctx->partials(), np, sc + 4, s));
+      CK(cudaMemcpyAsync(x, St, P * 4, cudaMemcpyDeviceToDevice, s));
+      CK(launch_scale(x, P, nullptr, sc + 4, s));
+    }
+  }
+  double h[4] = {0, 0, 0, 0};
+  CK(cudaMemcpyAsync(h, sc, 4 * sizeof(double), cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  ctx->beta_closed = h[0];
+  ctx->beta = 1.01 * h[2];
+  ctx->ws_norm2 = g.J > 0 ? 1.01 * h[3] : 1.0;
+  if (!std::isfinite(ctx->beta) || !(ctx->beta > 0)) return fail(ctx, MUFFIN_ERR_NONFINITE, "power method for beta failed");
+  compute_steps(ctx);
+  drop_graph(ctx);
+  ctx->state = 1;
+  return MUFFIN_OK;
+}
+
+int muffin_iterate(muffin_ctx* ctx, int n_iter) {
+  if (!ctx) return fail(nullptr, MUFFIN_ERR_ARG, "ctx is NULL");
+  if (n_iter < 0) return fail(ctx, MUFFIN_ERR_ARG, "n_iter < 0");
+  if (ctx->state < 1) return fail(ctx, MUFFIN_ERR_STATE, "muffin_set_psf must come before muffin_iterate");
+  if (n_iter == 0) return MUFFIN_OK;
+  if (!ctx->exec) {
+    CK(cudaStreamBeginCapture(ctx->cap, cudaStreamCaptureModeThreadLocal));
+    const int r = enqueue_pass(ctx, ctx->cap, nullptr);
+    cudaGraph_t gr = nullptr;
+    const cudaError_t e = cudaStreamEndCapture(ctx->cap, &gr);
+    if (r != MUFFIN_OK) { if (gr) cudaGraphDestroy(gr); return r; }
+    if (e != cudaSuccess) return fail(ctx, MUFFIN_ERR_CUDA, "cudaStreamEndCapture", cudaGetErrorString(e));
+    ctx->graph = gr;
+    CK(cudaGraphInstantiate(&ctx->exec, ctx->graph, 0));
+  }
+  for (int i = 0; i < n_iter; ++i) CK(cudaGraphLaunch(ctx->exec, ctx->stream));
+  ctx->iter += n_iter;
+  return MUFFIN_OK;
+}
+
+int muffin_iterate_timed(muffin_ctx* ctx, int n_iter, double* h_ms, int n_stages) {
+  if (!ctx) return fail(nullptr, MUFFIN_ERR_ARG, "ctx is NULL");
+  if (ctx->state < 1) return fail(ctx, MUFFIN_ERR_STATE, "muffin_set_psf must come before muffin_iterate_timed");
+  if (n_iter < 0 || (n_stages > 0 && !h_ms)) return fail(ctx, MUFFIN_ERR_ARG, "bad n_iter or h_ms");
+  std::vector<cudaEvent_t> ev;
+  std::vector<int> st;
+  StageTimer tm{&ev, &st, ctx->stream};
+  int r = MUFFIN_OK;
+  for (int i = 0; i < n_iter && r == MUFFIN_OK; ++i) r = enqueue_pass(ctx, ctx->stream, &tm);
+  cudaError_t e = cudaStreamSynchronize(ctx->stream);
+  for (int k = 0; k < n_stages; ++k) h_ms[k] = 0.0;
+  for (size_t i = 1; i < ev.size() && e == cudaSuccess; ++i) {
+    if (st[i] < 0) continue;
+    float ms = 0.f;
+    e = cudaEventElapsedTime(&ms, ev[i - 1], ev[i]);
+    if (st[i] < n_stages) h_ms[st[i]] += ms;
+  }
+  for (auto x : ev) cudaEventDestroy(x);
+  if (r != MUFFIN_OK) return r;
+  if (e != cudaSuccess) return fail(ctx, MUFFIN_ERR_CUDA, "timed iteration", cudaGetErrorString(e));
+  ctx->iter += n_iter;
+  return MUFFIN_OK;
+}
+
+int muffin_objective(muffin_ctx* ctx, double* h_obj, double* h_terms) {
+  if (!ctx) return fail(nullptr, MUFFIN_ERR_ARG, "ctx is NULL");
+  if (ctx->state < 1) return fail(ctx, MUFFIN_ERR_STATE, "muffin_set_psf must come before muffin_objective");
+  if (!h_obj) return fail(ctx, MUFFIN_ERR_ARG, "h_obj is NULL");
+  const Geom& g = ctx->g;
+  const Layout& lo = ctx->lo;
+  cudaStream_t s = ctx->stream;
+  double* sc = ctx->scal();
+  void* z = ctx->ws + lo.z64;
+  int np = 0;
+  CK(cudaMemsetAsync(sc + 10, 0, 4 * sizeof(double), s));
+  CK(launch_c2c_rows64(ctx->X(), 2, z, g.n, g.L, -1, ctx->ws + lo.twd, s));
+  CK(launch_cols64_fidelity(z, ctx->ws + lo.hhat, ctx->ws + lo.yhat, ctx->at<double>(lo.w), g.n, g.L,
+                            ctx->ws + lo.twd, ctx->partials(), &np, s));
+  CK(launch_sum_partials(ctx->partials(), np, sc + 10, s));
+  IuwtArgs ia{};
+  ia.D = ctx->X();
+  ia.U = ctx->U();
+  ia.cr = ctx->at<float>(lo.D);   // c_{j1} of X goes to scratch, not to the state
+  ia.partials = ctx->partials();
+  if (g.j1 > 0 || g.J == 0) {
+    CK(launch_fine_analysis(g, ia, MODE_NORM, s, &np));
+    CK(launch_sum_partials(ctx->partials(), np, sc + 11, s));
+  }
+  if (g.J > g.j1) {
+    const float* cin = g.j1 > 0 ? ctx->at<float>(lo.D) : ctx->X();
+    CK(launch_coarse(g, cin, nullptr, ctx->U(), 0.f, 1.f, MODE_NORM, ctx->partials(), s, &np));
+    CK(launch_sum_partials(ctx->partials(), np, sc + 12, s));
+  }
+  SpecArgs sa{};
+  sa.D = ctx->X();
+  sa.tw = ctx->at<float>(lo.twL);
+  sa.post = ctx->at<float>(lo.post);
+  sa.pre = ctx->at<float>(lo.pre);
+  sa.invs = ctx->at<float>(lo.invs);
+  sa.dense = ctx->at<float>(lo.dense);
+  sa.partials = ctx->partials();
+  CK(launch_spectral(sa, (int)ctx->P(), g.L, SPEC_NORM, s, &np));
+  CK(launch_sum_partials(ctx->partials(), np, sc + 13, s));
+  double h[4];
+  CK(cudaMemcpyAsync(h, sc + 10, sizeof(h), cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  const double data = h[0], sp = ctx->mu_s * (h[1] + h[2]), sl = ctx->mu_l * h[3];
+  *h_obj = data + sp + sl;
+  if (h_terms) { h_terms[0] = data; h_terms[1] = sp; h_terms[2] = sl; }
+  if (!std::isfinite(*h_obj)) return fail(ctx, MUFFIN_ERR_NONFINITE, "objective is not finite");
+  return MUFFIN_OK;
+}
+
+int muffin_get_cube(muffin_ctx* ctx, float* d_x) {
+  if (!ctx || !d_x) return fail(ctx, MUFFIN_ERR_ARG, "NULL argument");
+  CK(cudaMemcpyAsync(d_x, ctx->X(), ctx->vox() * 4, cudaMemcpyDeviceToDevice, ctx->stream));
+  return MUFFIN_OK;
+}
+
+int muffin_set_cube(muffin_ctx* ctx, const float* d_x) {
+  if (!ctx || !d_x) return fail(ctx, MUFFIN_ERR_ARG, "NULL argument");
+  CK(cudaMemcpyAsync(ctx->X(), d_x, ctx->vox() * 4, cudaMemcpyDeviceToDevice, ctx->stream));
+  return MUFFIN_OK;
+}
+
+int muffin_get_state(muffin_ctx* ctx, float* d_x, float* d_u, float* d_v, long long* h_iter) {
+  if (!ctx || !d_x || !d_u || !d_v) return fail(ctx, MUFFIN_ERR_ARG, "NULL argument");
+  const Geom& g = ctx->g;
+  CK(cudaMemcpyAsync(d_x, ctx->X(), ctx->vox() * 4, cudaMemcpyDeviceToDevice, ctx->stream));
+  CK(launch_permute_planes(ctx->U(), d_u, g.n, g.L, g.J, g.j1, 0, ctx->stream));
+  CK(cudaMemcpyAsync(d_v, ctx->V(), ctx->vox() * 4, cudaMemcpyDeviceToDevice, ctx->stream));
+  if (h_iter) *h_iter = ctx->iter;
+  return MUFFIN_OK;
+}
+
+int muffin_set_state(muffin_ctx* ctx, const float* d_x, const float* d_u, const float* d_v, long long iter) {
+  if (!ctx || !d_x || !d_u || !d_v) return fail(ctx, MUFFIN_ERR_ARG, "NULL argument");
+  if (ctx->state < 1) return fail(ctx, MUFFIN_ERR_STATE, "muffin_set_psf must come before muffin_set_state");
+  const Geom& g = ctx->g;
+  CK(cudaMemcpyAsync(ctx->X(), d_x, ctx->vox() * 4, cudaMemcpyDeviceToDevice, ctx->stream));
+  CK(launch_permute_planes(d_u, ctx->U(), g.n, g.L, g.J, g.j1, 1, ctx->stream));
+  CK(cudaMemcpyAsync(ctx->V(), d_v, ctx->vox() * 4, cudaMemcpyDeviceToDevice, ctx->stream));
+  const int r = refresh_adjoints(ctx);
+  if (r != MUFFIN_OK) return r;
+  ctx->iter = iter;
+  return MUFFIN_OK;
+}
+
+int muffin_set_mu(muffin_ctx* ctx, double mu_s, double mu_l) {
+  if (!ctx) return fail(nullptr, MUFFIN_ERR_ARG, "ctx is NULL");
+  if (!(mu_s >= 0) || !(mu_l >= 0) || !std::isfinite(mu_s) || !std::isfinite(mu_l))
+    return fail(ctx, MUFFIN_ERR_ARG, "mu_s and mu_l must be finite and >= 0");
+  ctx->mu_s = mu_s;
+  ctx->mu_l = mu_l;
+  if (ctx->state >= 1) compute_steps(ctx);
+  drop_graph(ctx);
+  return MUFFIN_OK;
+}
+
+int muffin_step_sizes(const muffin_ctx* ctx, double* tau, double* sigma, double* rho, double* beta, double* l_norm2,
+                      double* beta_closed, double* ws_norm2) {
+  if (!ctx) return MUFFIN_ERR_ARG;
+  if (ctx->state < 1) return MUFFIN_ERR_STATE;
+  if (tau) *tau = ctx->tau;
+  if (sigma) *sigma = ctx->sigma;
+  if (rho) *rho = ctx->rho;
+  if (beta) *beta = ctx->beta;
+  if (l_norm2) *l_norm2 = ctx->l_norm2;
+  if (beta_closed) *beta_closed = ctx->beta_closed;
+  if (ws_norm2) *ws_norm2 = ctx->ws_norm2;
+  return MUFFIN_OK;
+}
+
+int muffin_num_stages(void) { return kNumStages; }
+
+const char* muffin_stage_name(int k) { return (k >= 0 && k < kNumStages) ? kStageNames[k] : ""; }
+
+double muffin_stage_bytes(const muffin_ctx* ctx, int k) {
+  if (!ctx) return 0.0;
+  const Geom& g = ctx->g;
+  const double V = (double)ctx->vox();
+  const bool sp = ctx->mu_s != 0.0, sl = ctx->mu_l != 0.0;
+  switch (k) {
+    case 0: return (sp && g.J > 0 && g.j1 > 0) ? 4.0 * V * (g.j1 + 2) : 0.0;
+    case 1: return 8.0 * V;
+    case 2: return 8.0 * V + 4.0 * (double)g.L * g.n * (g.n / 2 + 1);
+    case 3: return V * (4 + 4 + (sp ? 4 : 0) + (sl ? 4 : 0) + 8 + 4);
+    case 4:
+      if (!sp || !(g.j1 > 0 || g.J == 0)) return 0.0;
+      return V * (4.0 + 8.0 * g.j1 + (g.J == g.j1 ? 8.0 : 4.0));
+    case 5: return (sp && g.J > g.j1) ? V * (4.0 + 8.0 * (g.J - g.j1 + 1) + 4.0) : 0.0;
+    case 6: return sl ? 16.0 * V : 0.0;
+  }
+  return 0.0;
+}
+
+int muffin_kernels_per_iteration(const muffin_ctx* ctx) {
+  if (!ctx) return 0;
+  int n = 0;
+  for (int k = 0; k < kNumStages; ++k) n += muffin_stage_bytes(ctx, k) > 0 ? 1 : 0;
+  return n;
+}
+
+const char* muffin_last_error(const muffin_ctx* ctx) { return ctx ? ctx->err.c_str() : g_init_error.c_str(); }
+
+void muffin_destroy(muffin_ctx* ctx) {
+  if (!ctx) return;
+  drop_graph(ctx);
+  if (ctx->cap) cudaStreamDestroy(ctx->cap);
+  delete ctx;
+}
+
+}  // extern "C"
