@@ -132,6 +132,24 @@ double muffin_stage_bytes(const muffin_ctx* ctx, int k);
 int muffin_kernels_per_iteration(const muffin_ctx* ctx);
 
 const char* muffin_last_error(const muffin_ctx* ctx);  /* ctx may be NULL (init errors) */
+
+/* Spectral l1 sum  sum_n ||W_lambda x^n||_1  of a device cube d_x [nchan][n_pix]
+ * (float32, channel-major), written as one double to d_out (device), for
+ * callers that cannot allocate device memory at all: code inside a host
+ * framework that owns every device byte through its own pool, a plugin handed
+ * fixed buffers, or a memory-capped service.  The paper has no counterpart;
+ * it is the third term of muffin_objective (divided by mu_lambda) computed by
+ * the same kernel, with its scratch (per-block partial sums and DCT tables)
+ * in one static device array of about 515 KiB that every GPU loading the
+ * library holds until the process exits.  Limits: 1 <= n_pix <= 2^20,
+ * 1 <= nchan <= 256; larger sizes return MUFFIN_ERR_ARG.  Calls no cudaMalloc
+ * or cudaFree.  The first call on each device looks up the array's device
+ * address (make that first call before any stream capture).  Every call
+ * shares the array and leaves its contents behind, so calls that overlap on
+ * the GPU (other streams, other host threads) race: serialise them.
+ * Asynchronous on stream; errors are described by muffin_noalloc_last_error. */
+int muffin_spectral_l1_noalloc(const float* d_x, int n_pix, int nchan, double* d_out, cudaStream_t stream);
+const char* muffin_noalloc_last_error(void);
 void muffin_destroy(muffin_ctx* ctx);
 
 #ifdef __cplusplus
