@@ -200,6 +200,7 @@ def main():
     ms_step = ms / args.steps
     value = voxels * world * args.steps / (ms / 1e3)
     launches = m.kernels_per_iteration() * args.steps
+    fine_levels, cluster = m.tiling()
 
     # per-stage device times over a second timed region (events between stages on the launching stream)
     names = [s for s in __import__("paper_1602_08847_gb300.muffin", fromlist=["stage_names"]).stage_names()]
@@ -239,7 +240,7 @@ def main():
             "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {"workload": WORKLOAD, "voxels_per_gpu": voxels, "nscales": J, "iuwt_gen": 1,
                        "l2": "inputs larger than L2 (state ~2.4 GB per cube)", "parallelism": f"replicas{world}",
-                       "graph": True},
+                       "graph": True, "iuwt_fine_levels": fine_levels, "iuwt_cluster": cluster},
             "roofline": roofline, "gpu_launches": launches, "clocks": clk.summary()}
 
     # end to end through the public call: pinned host cubes in, X back to host

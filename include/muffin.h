@@ -130,6 +130,10 @@ const char* muffin_stage_name(int k);
 double muffin_stage_bytes(const muffin_ctx* ctx, int k);
 /* Number of kernels one pass of Algorithm 1 launches for this context. */
 int muffin_kernels_per_iteration(const muffin_ctx* ctx);
+/* Wavelet tiling in use: levels j < *fine_levels run on halo tiles, the others
+ * on class sub-images split over *cluster blocks (0: single-block streaming
+ * kernel).  Either pointer may be NULL. */
+int muffin_tiling(const muffin_ctx* ctx, int* fine_levels, int* cluster);
 
 const char* muffin_last_error(const muffin_ctx* ctx);  /* ctx may be NULL (init errors) */
 

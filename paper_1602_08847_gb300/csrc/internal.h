@@ -13,6 +13,7 @@ struct Geom {
   int J;        // IUWT detail scales
   int gen;      // IUWT generation (1 or 2)
   int j1;       // fine levels computed on halo tiles; levels >= j1 run class-permuted
+  int cs;       // blocks per cluster of the coarse kernel (0: single-block streaming kernel)
 };
 
 // ---- FFT path (k_fft.cu) ----
@@ -58,11 +59,17 @@ struct IuwtArgs {
 };
 size_t fine_smem_bytes(const Geom& g, int adjoint);
 size_t coarse_smem_bytes(const Geom& g);
+// host-only size estimates used to choose the split j1 (no CUDA calls)
+size_t fine_smem_bytes(int gen, int j1, int adjoint);
+size_t coarse_cl_smem_bytes(int n, int J, int gen, int j1, int cs);
+size_t coarse_stream_smem_bytes(int n, int gen, int j1);
+int coarse_cluster_size(int n, int J, int gen, int j1, size_t budget);
 cudaError_t launch_fine_analysis(const Geom& g, const IuwtArgs& a, int mode, cudaStream_t s, int* nblocks);
 cudaError_t launch_fine_adjoint(const Geom& g, const IuwtArgs& a, cudaStream_t s);
 cudaError_t launch_coarse(const Geom& g, const float* c_in, float* r_out, float* U, float k, float rho, int mode,
                           double* partials, cudaStream_t s, int* nblocks);
-cudaError_t iuwt_configure(const Geom& g);
+// Opt the wavelet kernels into shared memory and pick g.cs for this device.
+cudaError_t iuwt_configure(Geom& g);
 cudaError_t fft_configure(int n);
 
 // ---- spectral step (k_spectral.cu) ----

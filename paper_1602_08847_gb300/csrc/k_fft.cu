@@ -19,7 +19,7 @@
 namespace muffin {
 
 template <int N> __host__ __device__ constexpr int rows_pairs() { return (2048 / N) < (N / 2) ? (2048 / N) : (N / 2); }
-template <int N> __host__ __device__ constexpr int cols_per_cta() { return N >= 1024 ? 8 : ((N / 2) < 16 ? (N / 2) : 16); }
+template <int N> __host__ __device__ constexpr int cols_per_cta() { return N >= 512 ? 8 : ((N / 2) < 16 ? (N / 2) : 16); }
 
 // ------------------------------------------------------------------ FP32 rows forward
 template <int N>

@@ -6,10 +6,11 @@
 //
 // One block handles 32 consecutive pixels (one per lane) and all L channels;
 // reads and writes of D, V and T are coalesced along the pixels.
-//  * L a power of two in [16, 256]: Makhoul's O(L log L) DCT through a
-//    length-L complex FFT (reorder x -> v with v[m] = x[2m], v[L-1-m] =
-//    x[2m+1]; DCT[k] = Re(exp(-i pi k / 2L) FFT(v)[k]); the inverse runs the
-//    same steps backwards).  Warp w is FFT thread w of all 32 transforms.
+//  * L a power of two in [16, 256]: Makhoul's O(L log L) DCT (reorder x -> v
+//    with v[m] = x[2m], v[L-1-m] = x[2m+1]; DCT[k] = Re(exp(-i pi k / 2L)
+//    FFT(v)[k]); the inverse runs the same steps backwards), the real FFT of
+//    length L done as one complex FFT of length L/2.  Warp w is FFT thread w
+//    of all 32 transforms.
 //  * other L (<= 512): the dense orthonormal DCT matrix.
 #include "device.cuh"
 #include "internal.h"
@@ -20,51 +21,81 @@ bool spectral_uses_fft(int L) { return L >= 16 && L <= 256 && (L & (L - 1)) == 0
 
 __device__ __forceinline__ int makhoul_src(int m, int L) { return m < L / 2 ? 2 * m : 2 * (L - 1 - m) + 1; }
 
+// Power-of-two L: the reordered sequence v is real, so its length-L FFT comes
+// from one length-L/2 complex FFT of z[m] = v[2m] + i v[2m+1] (even/odd
+// split: V[k] = E[k] + w^k O[k], V[k + L/2] = E[k] - w^k O[k], w = e^{-2 pi i/L},
+// E and O recovered from Z[k] and conj Z[L/2 - k]); the inverse runs the same
+// split backwards.  Thread (lane, t) owns coefficients k and k + L/2 for
+// k = t + q L/16, q < 8.
 template <int L, int MODE>
-__global__ void __launch_bounds__(4 * L)
+__global__ void __launch_bounds__(2 * L, 2)
 k_spectral_fft(SpecArgs a, int npix) {
-  const float* __restrict__ invs = a.invs;
-  constexpr int T8 = L / 8;
+  constexpr int H = L / 2, T16 = L / 16;
   extern __shared__ __align__(16) unsigned char smraw[];
-  cpx<float>* work = reinterpret_cast<cpx<float>*>(smraw);        // [L][32]
-  float* vb = reinterpret_cast<float*>(work + L * 32);            // [L][32]
-  cpx<float>* tw = reinterpret_cast<cpx<float>*>(vb + L * 32);
+  cpx<float>* work = reinterpret_cast<cpx<float>*>(smraw);        // [H][32]
+  float* vb = reinterpret_cast<float*>(work + H * 32);            // [L][32]
+  cpx<float>* twh = reinterpret_cast<cpx<float>*>(vb + L * 32);   // [H], e^{-2 pi i m / H}
   __shared__ double red[32];
+  const cpx<float>* twl = reinterpret_cast<const cpx<float>*>(a.tw);   // e^{-2 pi i m / L}
+  const cpx<float>* post = reinterpret_cast<const cpx<float>*>(a.post);
+  const cpx<float>* pre = reinterpret_cast<const cpx<float>*>(a.pre);
   const int lane = threadIdx.x, t = threadIdx.y;
-  const int tid = t * 32 + lane, nth = 32 * T8;
-  for (int i = tid; i < L; i += nth) tw[i] = reinterpret_cast<const cpx<float>*>(a.tw)[i];
+  const int tid = t * 32 + lane, nth = 32 * T16;
+  for (int i = tid; i < H; i += nth) twh[i] = twl[2 * i];
   const int pix = blockIdx.x * 32 + lane;
   const bool ok = pix < npix;
   const size_t P = (size_t)npix;
-  cpx<float> v[8];
+  cpx<float> z[8];
   double acc = 0.0;
-  if (MODE != SPEC_TONLY) {
+  if constexpr (MODE != SPEC_TONLY) {
+    float vold[16];
 #pragma unroll
     for (int q = 0; q < 8; ++q) {
-      const int mpos = t + q * T8;
-      v[q] = mk<float>(ok ? __ldg(a.D + (size_t)makhoul_src(mpos, L) * P + pix) : 0.0f, 0.0f);
+      const int m = t + q * T16;
+      z[q] = ok ? mk<float>(__ldg(a.D + (size_t)makhoul_src(2 * m, L) * P + pix),
+                            __ldg(a.D + (size_t)makhoul_src(2 * m + 1, L) * P + pix))
+                : mk<float>(0.0f, 0.0f);
     }
     __syncthreads();
-    fft_regs<float, L, -1, 32>(v, work + lane, tw, t);
+    fft_regs<float, H, -1, 32>(z, work + lane, twh, t);
+    // the old duals arrive while the spectrum is exchanged through shared memory
+    if constexpr (MODE == SPEC_UPDATE) {
 #pragma unroll
-    for (int q = 0; q < 8; ++q) {
-      const int kk = t + q * T8;
-      const cpx<float> pw = reinterpret_cast<const cpx<float>*>(a.post)[kk];
-      const float cdct = pw.x * v[q].x - pw.y * v[q].y;   // Re(post[k] V[k]), orthonormal scale folded in
-      if (MODE == SPEC_NORM) {
-        acc += fabs((double)cdct);
-      } else if (ok) {
-        float* vp = a.V + (size_t)kk * P + pix;
-        const float vo = *vp;
-        const float vt = sat1(vo + a.k * cdct);
-        const float vn = a.rho * vt + (1.0f - a.rho) * vo;
-        *vp = vn;
-        vb[kk * 32 + lane] = vn * invs[kk];
-      } else {
-        vb[kk * 32 + lane] = 0.0f;
+      for (int q = 0; q < 8; ++q) {
+        const int m = t + q * T16;
+        vold[q] = ok ? a.V[(size_t)m * P + pix] : 0.0f;
+        vold[q + 8] = ok ? a.V[(size_t)(m + H) * P + pix] : 0.0f;
       }
     }
-    if (MODE == SPEC_NORM) {
+    __syncthreads();
+#pragma unroll
+    for (int q = 0; q < 8; ++q) work[(t + q * T16) * 32 + lane] = z[q];
+    __syncthreads();
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+      const int k = t + q * T16;
+      const cpx<float> zk = z[q], zm = conj(work[((H - k) & (H - 1)) * 32 + lane]);
+      const cpx<float> e = scale(add(zk, zm), 0.5f);
+      const cpx<float> d = sub(zk, zm);
+      const cpx<float> o = mk<float>(0.5f * d.y, -0.5f * d.x);      // (zk - zm) / 2i
+      const cpx<float> wo = mul(twl[k], o);
+      const cpx<float> v0 = add(e, wo), v1 = sub(e, wo);
+      const cpx<float> p0 = post[k], p1 = post[k + H];
+      const float c0 = p0.x * v0.x - p0.y * v0.y, c1 = p1.x * v1.x - p1.y * v1.y;
+      if constexpr (MODE == SPEC_NORM) {
+        acc += fabs((double)c0) + fabs((double)c1);
+      } else {
+        const float n0 = a.rho * sat1(vold[q] + a.k * c0) + (1.0f - a.rho) * vold[q];
+        const float n1 = a.rho * sat1(vold[q + 8] + a.k * c1) + (1.0f - a.rho) * vold[q + 8];
+        if (ok) {
+          a.V[(size_t)k * P + pix] = n0;
+          a.V[(size_t)(k + H) * P + pix] = n1;
+        }
+        vb[k * 32 + lane] = ok ? n0 * a.invs[k] : 0.0f;
+        vb[(k + H) * 32 + lane] = ok ? n1 * a.invs[k + H] : 0.0f;
+      }
+    }
+    if constexpr (MODE == SPEC_NORM) {
       const double tot = block_sum(acc, red);
       if (tid == 0) a.partials[blockIdx.x] = tot;
       return;
@@ -72,26 +103,31 @@ k_spectral_fft(SpecArgs a, int npix) {
   } else {
 #pragma unroll
     for (int q = 0; q < 8; ++q) {
-      const int kk = t + q * T8;
-      vb[kk * 32 + lane] = ok ? __ldg(a.V + (size_t)kk * P + pix) * invs[kk] : 0.0f;
+      const int k = t + q * T16;
+      vb[k * 32 + lane] = ok ? __ldg(a.V + (size_t)k * P + pix) * a.invs[k] : 0.0f;
+      vb[(k + H) * 32 + lane] = ok ? __ldg(a.V + (size_t)(k + H) * P + pix) * a.invs[k + H] : 0.0f;
     }
   }
   __syncthreads();
-  // inverse: W[k] = pre[k] (y[k] - i y[L-k]), y[L] = 0, then an inverse FFT
+  // inverse: W[k] = pre[k] (y[k] - i y[L-k]) with y[L] = 0, folded to half length
 #pragma unroll
   for (int q = 0; q < 8; ++q) {
-    const int kk = t + q * T8;
-    const float yr = vb[kk * 32 + lane];
-    const float yi = kk == 0 ? 0.0f : vb[(L - kk) * 32 + lane];
-    const cpx<float> pw = reinterpret_cast<const cpx<float>*>(a.pre)[kk];
-    v[q] = mul(pw, mk<float>(yr, -yi));
+    const int k = t + q * T16;
+    const float ya = vb[k * 32 + lane], yb = k == 0 ? 0.0f : vb[(L - k) * 32 + lane];
+    const float yc = vb[(k + H) * 32 + lane], yd = vb[(H - k) * 32 + lane];
+    const cpx<float> w0 = mul(pre[k], mk<float>(ya, -yb));
+    const cpx<float> w1 = mul(pre[k + H], mk<float>(yc, -yd));
+    const cpx<float> A = add(w0, w1);
+    const cpx<float> B = mul(sub(w0, w1), conj(twl[k]));
+    z[q] = mk<float>(A.x - B.y, A.y + B.x);                          // A + i B
   }
-  fft_regs<float, L, 1, 32>(v, work + lane, tw, t);
+  fft_regs<float, H, 1, 32>(z, work + lane, twh, t);
   if (ok) {
 #pragma unroll
     for (int q = 0; q < 8; ++q) {
-      const int mpos = t + q * T8;
-      a.T[(size_t)makhoul_src(mpos, L) * P + pix] = v[q].x;
+      const int m = t + q * T16;
+      a.T[(size_t)makhoul_src(2 * m, L) * P + pix] = z[q].x;
+      a.T[(size_t)makhoul_src(2 * m + 1, L) * P + pix] = z[q].y;
     }
   }
 }
@@ -146,11 +182,11 @@ k_spectral_dense(SpecArgs a, int npix, int L) {
 }
 
 template <int L> static size_t fft_smem() {
-  return (size_t)L * 32 * sizeof(cpx<float>) + (size_t)L * 32 * sizeof(float) + (size_t)L * sizeof(cpx<float>);
+  return (size_t)(L / 2) * 32 * sizeof(cpx<float>) + (size_t)L * 32 * sizeof(float) + (size_t)(L / 2) * sizeof(cpx<float>);
 }
 
 template <int L> static cudaError_t spec_fft(const SpecArgs& a, int npix, int mode, cudaStream_t s) {
-  dim3 grid((npix + 31) / 32), block(32, L / 8);
+  dim3 grid((npix + 31) / 32), block(32, L / 16);
   switch (mode) {
     case SPEC_UPDATE: k_spectral_fft<L, SPEC_UPDATE><<<grid, block, fft_smem<L>(), s>>>(a, npix); break;
     case SPEC_NORM: k_spectral_fft<L, SPEC_NORM><<<grid, block, fft_smem<L>(), s>>>(a, npix); break;

@@ -16,7 +16,6 @@ using namespace muffin;
 namespace {
 
 thread_local std::string g_init_error;
-constexpr int kMaxSmem = 232448;   // dynamic shared memory a block may opt into on sm_100/sm_103
 constexpr int kNumStages = 7;
 const char* kStageNames[kNumStages] = {"iuwt_fine_adjoint", "fft_rows_fwd", "fft_cols_filter", "fft_rows_inv_primal",
                                        "iuwt_fine_analysis", "iuwt_coarse", "spectral_dct"};
@@ -24,20 +23,34 @@ const char* kStageNames[kNumStages] = {"iuwt_fine_adjoint", "fft_rows_fwd", "fft
 bool is_pow2(int v) { return v > 0 && (v & (v - 1)) == 0; }
 int ilog2(int v) { int r = 0; while ((1 << r) < v) ++r; return r; }
 
-size_t coarse_bytes(int n, int gen, int j1) {
-  const size_t M = (size_t)(n >> j1);
-  return (gen == 1 ? 2 : 3) * M * M * sizeof(float);
-}
-
-// Smallest split j1 whose coarse sub-images fit in shared memory.
+// Split j1 (levels below it run on halo tiles, the others on class
+// sub-images).  Measured on GB300: the largest split whose coarse sub-image
+// fits one block within 110 KB wins (fewer barriers, no cluster exchange);
+// failing that, the smallest split that fits a cluster, then the streaming
+// kernel.  -1 if nothing fits.
 int auto_j1(int n, int J, int gen) {
   if (J == 0) return 0;
   const int top = J < 3 ? J : 3;
+  for (int j1 = top; j1 >= 0; --j1) {
+    if (j1 > 0 && n < 64) continue;
+    if (J > j1 && coarse_cl_smem_bytes(n, J, gen, j1, 1) <= 110 * 1024) return j1;
+  }
+  for (size_t budget : {(size_t)110 * 1024, (size_t)220 * 1024}) {
+    for (int j1 = 0; j1 <= top; ++j1) {
+      if (j1 > 0 && n < 64) break;
+      if (J == j1 || coarse_cluster_size(n, J, gen, j1, budget) > 0) return j1;
+    }
+  }
   for (int j1 = 0; j1 <= top; ++j1) {
     if (j1 > 0 && n < 64) break;
-    if (J == j1 || coarse_bytes(n, gen, j1) <= 200 * 1024) return j1;
+    if (J == j1 || coarse_stream_smem_bytes(n, gen, j1) <= 200 * 1024) return j1;
   }
   return -1;
+}
+
+bool split_fits(int n, int J, int gen, int j1) {
+  if (J == j1) return true;
+  return coarse_cluster_size(n, J, gen, j1, 220 * 1024) > 0 || coarse_stream_smem_bytes(n, gen, j1) <= 220 * 1024;
 }
 
 int check(const muffin_params* p, std::string* why) {
@@ -64,7 +77,7 @@ int check(const muffin_params* p, std::string* why) {
     const int top = p->nscales < 3 ? p->nscales : 3;
     if (j1 > top) return fail("fine_levels must be <= min(J, 3)");
     if (j1 > 0 && p->nx < 64) return fail("fine_levels > 0 needs N >= 64");
-    if (p->nscales > j1 && coarse_bytes(p->nx, p->iuwt_gen, j1) > (size_t)kMaxSmem)
+    if (!split_fits(p->nx, p->nscales, p->iuwt_gen, j1))
       return fail("fine_levels too small: coarse sub-image does not fit shared memory");
   }
   return MUFFIN_OK;
@@ -342,7 +355,7 @@ int muffin_init(muffin_ctx** out, const muffin_params* p, const float* d_dirty, 
   ctx->p = *p;
   ctx->p.h_chan_weight = nullptr;
   ctx->lo = lo;
-  ctx->g = Geom{p->nx, p->nchan, p->nscales, p->iuwt_gen, lo.j1};
+  ctx->g = Geom{p->nx, p->nchan, p->nscales, p->iuwt_gen, lo.j1, 0};
   ctx->stream = stream;
   ctx->ws = reinterpret_cast<char*>(d_workspace);
   ctx->w.assign(p->nchan, 1.0);
@@ -663,6 +676,13 @@ int muffin_kernels_per_iteration(const muffin_ctx* ctx) {
   int n = 0;
   for (int k = 0; k < kNumStages; ++k) n += muffin_stage_bytes(ctx, k) > 0 ? 1 : 0;
   return n;
+}
+
+int muffin_tiling(const muffin_ctx* ctx, int* fine_levels, int* cluster) {
+  if (!ctx) return MUFFIN_ERR_ARG;
+  if (fine_levels) *fine_levels = ctx->g.j1;
+  if (cluster) *cluster = ctx->g.cs;
+  return MUFFIN_OK;
 }
 
 const char* muffin_last_error(const muffin_ctx* ctx) { return ctx ? ctx->err.c_str() : g_init_error.c_str(); }

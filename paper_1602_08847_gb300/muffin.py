@@ -60,6 +60,7 @@ def _load():
         "muffin_stage_name": (ctypes.c_char_p, [I]),
         "muffin_stage_bytes": (D, [P, I]),
         "muffin_kernels_per_iteration": (I, [P]),
+        "muffin_tiling": (I, [P, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int)]),
         "muffin_last_error": (ctypes.c_char_p, [P]),
         "muffin_destroy": (V, [P]),
     }
@@ -207,6 +208,11 @@ class Muffin:
 
     def kernels_per_iteration(self) -> int:
         return int(_lib.muffin_kernels_per_iteration(self._ctx))
+
+    def tiling(self) -> tuple[int, int]:
+        j1, cs = ctypes.c_int(), ctypes.c_int()
+        self._check(_lib.muffin_tiling(self._ctx, ctypes.byref(j1), ctypes.byref(cs)))
+        return j1.value, cs.value
 
     def close(self):
         if getattr(self, "_ctx", None) and self._ctx.value:
