@@ -75,26 +75,29 @@ k_cols_filter(cpx<float>* __restrict__ spec, const float* __restrict__ Kp, const
   const int kx = blockIdx.x * C + c;
   cpx<float>* base = spec + (size_t)l * N * H;
   cpx<float> v[8];
+  float ka[8], kb[8];
+  const float* Kl = Kp + (size_t)l * N * H;
 #pragma unroll
-  for (int q = 0; q < 8; ++q) v[q] = base[(t + q * T8) * H + kx];
+  for (int q = 0; q < 8; ++q) {
+    v[q] = base[(t + q * T8) * H + kx];
+    ka[q] = __ldg(Kl + (t + q * T8) * H + kx);   // multipliers arrive during the forward FFT
+    kb[q] = kx == 0 ? __ldg(Kb + (size_t)l * N + t + q * T8) : 0.0f;
+  }
   __syncthreads();
   fft_regs<float, N, -1, C>(v, buf + c, tw, t);
   __syncthreads();
 #pragma unroll
   for (int q = 0; q < 8; ++q) buf[(t + q * T8) * C + c] = v[q];
   __syncthreads();
-  const float* Kl = Kp + (size_t)l * N * H;
 #pragma unroll
   for (int q = 0; q < 8; ++q) {
     const int pos = t + q * T8;
-    const float a = __ldg(Kl + pos * H + kx);
     if (kx == 0) {
       // (DC, Nyquist) packed column: Z'(k) = a Z(k) + b conj(Z(-k))
       const cpx<float> zm = buf[((N - pos) & (N - 1)) * C + c];
-      const float bq = __ldg(Kb + (size_t)l * N + pos);
-      v[q] = add(scale(v[q], a), scale(conj(zm), bq));
+      v[q] = add(scale(v[q], ka[q]), scale(conj(zm), kb[q]));
     } else {
-      v[q] = scale(v[q], a);
+      v[q] = scale(v[q], ka[q]);
     }
   }
   fft_regs<float, N, 1, C>(v, buf + c, tw, t);
@@ -104,7 +107,7 @@ k_cols_filter(cpx<float>* __restrict__ spec, const float* __restrict__ Kp, const
 
 // ------------------------------------------------------------------ FP32 rows inverse + primal
 template <int N, int MODE>
-__global__ void __launch_bounds__(rows_pairs<N>() * (N / 8))
+__global__ void __launch_bounds__(rows_pairs<N>() * (N / 8), 2)
 k_rows_inv(const cpx<float>* __restrict__ spec, PrimalArgs a, float* __restrict__ out,
            const cpx<float>* __restrict__ twg) {
   constexpr int T8 = N / 8, PAIRS = rows_pairs<N>(), H = N / 2;
@@ -134,9 +137,26 @@ k_rows_inv(const cpx<float>* __restrict__ spec, PrimalArgs a, float* __restrict_
       v[q] = mk<float>(A.x + B.y, B.x - A.y);
     }
   }
+  const size_t row0 = ((size_t)l * N + y0) * N;
+  // epilogue inputs of this thread's 16 pixels, loaded before the FFT so that
+  // their latency hides behind it: xo = X, bo = tau (mu_s S + mu_l T - b)
+  float xo[16], bo[16];
+  if constexpr (MODE == 0) {
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        const size_t idx = row0 + (size_t)h * N + t + q * T8;
+        xo[2 * q + h] = a.X[idx];
+        float st = -__ldg(a.b + idx);
+        if (a.S) st += a.mu_s * __ldg(a.S + idx);
+        if (a.T) st += a.mu_l * __ldg(a.T + idx);
+        bo[2 * q + h] = st;
+      }
+    }
+  }
   __syncthreads();
   fft_regs<float, N, 1, 1>(v, buf + f * N, tw, t);
-  const size_t row0 = ((size_t)l * N + y0) * N;
 #pragma unroll
   for (int q = 0; q < 8; ++q) {
     const int x = t + q * T8;
@@ -144,14 +164,11 @@ k_rows_inv(const cpx<float>* __restrict__ spec, PrimalArgs a, float* __restrict_
     for (int h = 0; h < 2; ++h) {
       const size_t idx = row0 + (size_t)h * N + x;
       const float g = h == 0 ? v[q].x : v[q].y;
-      if (MODE == 0) {
-        float step = g - __ldg(a.b + idx);
-        if (a.S) step += a.mu_s * __ldg(a.S + idx);
-        if (a.T) step += a.mu_l * __ldg(a.T + idx);
-        const float xo = a.X[idx];
-        const float xt = fmaxf(xo - a.tau * step, 0.0f);
-        a.D[idx] = 2.0f * xt - xo;
-        a.X[idx] = a.rho * xt + (1.0f - a.rho) * xo;
+      if constexpr (MODE == 0) {
+        const float x0 = xo[2 * q + h];
+        const float xt = fmaxf(x0 - a.tau * (g + bo[2 * q + h]), 0.0f);
+        a.D[idx] = 2.0f * xt - x0;
+        a.X[idx] = a.rho * xt + (1.0f - a.rho) * x0;
       } else {
         out[idx] = g;
       }

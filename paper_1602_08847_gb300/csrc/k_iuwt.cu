@@ -111,22 +111,27 @@ template <int GEN, int J1> struct FineGeo {
   static constexpr int HM = halo_max(GEN, J1);
   static constexpr int SD = kTile + 2 * HM;      // region side
   static constexpr int PA = SD + 1;              // pitch of natural-layout buffers (odd)
-  static constexpr int RA = SD + kQ;             // rows allocated (window overrun)
-  static constexpr int PT = SD + kQ + 1;         // pitch of the transposed buffer (odd)
+  static constexpr int RA = SD;                  // rows allocated
+  static constexpr int PT = SD + 1;              // pitch of the transposed buffer (odd)
   static constexpr int PI = kTile + 1;           // pitch of the interior buffer
   static constexpr int NA = RA * PA, NT = RA * PT, NI = kTile * PI;
 };
 
 // pass 1: vertical filter of X over rows of region eo, columns of region ei -> T (transposed)
+// The last window of a row or column is moved back to end on the region's
+// edge (regions are at least kQ wide), so no window reads or writes past the
+// buffers; outputs it shares with the previous window are written once.
 template <int HM, int PA, int PT, int D>
 __device__ __forceinline__ void fine_pass1(const float* __restrict__ X, float* __restrict__ T, int ei, int eo) {
-  const int ncol = kTile + 2 * ei, nseg = (kTile + 2 * eo + kQ - 1) / kQ;
+  const int ncol = kTile + 2 * ei, nseg = (kTile + 2 * eo + kQ - 1) / kQ, rend = HM + kTile + eo;
   for (int it = threadIdx.x; it < ncol * nseg; it += blockDim.x) {
-    const int c = HM - ei + it % ncol, r0 = HM - eo + (it / ncol) * kQ;
+    const int c = HM - ei + it % ncol, r0o = HM - eo + (it / ncol) * kQ;
+    const int r0 = r0o + kQ <= rend ? r0o : rend - kQ;
     float o[kQ];
     win<D>(X + r0 * PA + c, PA, o);
 #pragma unroll
-    for (int i = 0; i < kQ; ++i) T[c * PT + r0 + i] = o[i];
+    for (int i = 0; i < kQ; ++i)
+      if (r0 + i >= r0o) T[c * PT + r0 + i] = o[i];
   }
 }
 
@@ -135,12 +140,13 @@ template <int HM, int PT, int D, typename F>
 __device__ __forceinline__ void fine_pass2(const float* __restrict__ T, int er, int ec, F&& epi) {
   const int nrow = kTile + 2 * er, ncs = (kTile + 2 * ec + kQ - 1) / kQ, cend = HM + kTile + ec;
   for (int it = threadIdx.x; it < nrow * ncs; it += blockDim.x) {
-    const int r = HM - er + it % nrow, c0 = HM - ec + (it / nrow) * kQ;
+    const int r = HM - er + it % nrow, c0o = HM - ec + (it / nrow) * kQ;
+    const int c0 = c0o + kQ <= cend ? c0o : cend - kQ;
     float o[kQ];
     win<D>(T + c0 * PT + r, PT, o);
 #pragma unroll
     for (int i = 0; i < kQ; ++i)
-      if (c0 + i < cend) epi(r, c0 + i, o[i]);
+      if (c0 + i >= c0o) epi(r, c0 + i, o[i]);
   }
 }
 
@@ -176,11 +182,25 @@ __device__ __forceinline__ void load_region_class(float* __restrict__ X, const f
   }
 }
 
-// Interior pixel k (0..7) of this thread: row, column inside the 64 x 64 tile.
-__device__ __forceinline__ int int_row(int k) { return (int)threadIdx.x / kTile + (kFineThreads / kTile) * k; }
+// Square region of side S (compile time, <= 128) centred on the tile: warps
+// take rows, lanes take columns, f(r, c) with region-relative r, c.
+template <int S, typename F>
+__device__ __forceinline__ void region_for(F&& f) {
+  const int lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+  for (int r = threadIdx.x >> 5; r < S; r += nw) {
+#pragma unroll
+    for (int q = 0; q < (S + 31) / 32; ++q) {
+      const int c = lane + 32 * q;
+      if (c < S) f(r, c);
+    }
+  }
+}
+
+// Interior pixel k (k < 4096 / NT) of this thread: row, column inside the 64 x 64 tile.
+template <int NT> __device__ __forceinline__ int int_row(int k) { return (int)threadIdx.x / kTile + (NT / kTile) * k; }
 __device__ __forceinline__ int int_col() { return (int)threadIdx.x % kTile; }
 
-template <int GEN, int J1, int MODE, int J0>
+template <int GEN, int J1, int MODE, int J0, int NTH = kFineThreads>
 __device__ __forceinline__ void fine_analysis_level(float*& A, float*& B, float* T, float* Bi, float (&up)[J1 + 1][8],
                                                     const IuwtArgs& a, int n, int J, int l, int ty0, int tx0,
                                                     double& acc) {
@@ -207,7 +227,7 @@ __device__ __forceinline__ void fine_analysis_level(float*& A, float*& B, float*
   const int ci = int_col();
 #pragma unroll
   for (int k = 0; k < 8; ++k) {
-    const int ri = int_row(k);
+    const int ri = int_row<NTH>(k);
     const int i = (HM + ri) * PA + HM + ci;
     const float v = Bi[ri * PI + ci];
     dual_update_pf<MODE>(Uj + (size_t)(ty0 + ri) * n + (tx0 + ci), up[J0][k], A[i] - v, a.k, a.rho, acc);
@@ -221,6 +241,7 @@ __device__ __forceinline__ void fine_analysis_level(float*& A, float*& B, float*
 template <int GEN, int J1, int MODE>
 __global__ void __launch_bounds__(kFineThreads)
 k_fine_analysis(int n, int J, IuwtArgs a) {
+  constexpr int NTH = kFineThreads;
   using G = FineGeo<GEN, J1>;
   constexpr int HM = G::HM, SD = G::SD, PA = G::PA;
   extern __shared__ __align__(16) float sm[];
@@ -238,7 +259,7 @@ k_fine_analysis(int n, int J, IuwtArgs a) {
   const int ci = int_col();
 #pragma unroll
   for (int k = 0; k < 8; ++k) {
-    const int ri = int_row(k);
+    const int ri = int_row<NTH>(k);
 #pragma unroll
     for (int j = 0; j <= J1; ++j) up[j][k] = 0.0f;
     if constexpr (MODE == MODE_UPDATE) {
@@ -254,7 +275,7 @@ k_fine_analysis(int n, int J, IuwtArgs a) {
   // c_{j1} on the tile: last plane (J == j1) or hand-off to the coarse levels
 #pragma unroll
   for (int k = 0; k < 8; ++k) {
-    const int ri = int_row(k);
+    const int ri = int_row<NTH>(k);
     const int gy = ty0 + ri, gx = tx0 + ci;
     const int cidx = class_index(gy, gx, n, J1);
     const float cv = A[(HM + ri) * PA + HM + ci];
@@ -268,36 +289,39 @@ k_fine_analysis(int n, int J, IuwtArgs a) {
 }
 
 // ------------------------------------------------------------------ fine adjoint
-template <int GEN, int J1, int J0>
+template <int GEN, int J1, int J0, int NTH>
 __device__ __forceinline__ void fine_adjoint_level(float*& R, float*& Ub, float* T, const IuwtArgs& a, int n, int J,
                                                    int l, int ty0, int tx0) {
   using G = FineGeo<GEN, J1>;
   constexpr int HM = G::HM, PA = G::PA, PT = G::PT, D = 1 << J0;
   constexpr int er = halo_r(J0 + 1), en = halo_r(J0), eu = halo_u(GEN, J0);
-  // prefetch u_{J0-1} for the next level into registers while this level filters
+  // prefetch u_{J0-1} for the next level into registers while this level filters:
+  // thread (warp w, lane) takes rows w + NW k and columns lane + 32 q of that region
   constexpr int eun = J0 > 0 ? halo_u(GEN, J0 - 1) : 0;
-  constexpr int sidn = kTile + 2 * eun, NPF = J0 > 0 ? (sidn * sidn + kFineThreads - 1) / kFineThreads : 1;
-  float pf[NPF];
-  const size_t P = (size_t)n * n;
+  constexpr int sidn = kTile + 2 * eun, NW = NTH / 32;
+  constexpr int NR = J0 > 0 ? (sidn + NW - 1) / NW : 1, NQ = J0 > 0 ? (sidn + 31) / 32 : 1;
+  float pf[NR][NQ];
+  const int lane = threadIdx.x & 31, wrp = threadIdx.x >> 5;
   const int m = n - 1;
   if constexpr (J0 > 0) {
-    const float* Un = a.U + ((size_t)l * (J + 1) + J0 - 1) * P;
+    const float* Un = a.U + ((size_t)l * (J + 1) + J0 - 1) * (size_t)n * n;
 #pragma unroll
-    for (int q = 0; q < NPF; ++q) {
-      const int i = threadIdx.x + q * kFineThreads;
-      pf[q] = 0.0f;
-      if (i < sidn * sidn) {
-        const int r = i / sidn, c = i - r * sidn;
-        pf[q] = __ldg(Un + (size_t)((ty0 - eun + r) & m) * n + ((tx0 - eun + c) & m));
+    for (int k = 0; k < NR; ++k) {
+      const int r = wrp + NW * k;
+      const float* srow = Un + (size_t)((ty0 - eun + r) & m) * n;
+#pragma unroll
+      for (int q = 0; q < NQ; ++q) {
+        const int c = lane + 32 * q;
+        pf[k][q] = (r < sidn && c < sidn) ? __ldg(srow + ((tx0 - eun + c) & m)) : 0.0f;
       }
     }
   }
   if constexpr (GEN == 1) {
     constexpr int side = kTile + 2 * er;
-    for (int i = threadIdx.x; i < side * side; i += blockDim.x) {
-      const int r = HM - er + i / side, c = HM - er + i % side;
-      R[r * PA + c] -= Ub[r * PA + c];
-    }
+    region_for<side>([&](int r, int c) {
+      const int i = (HM - er + r) * PA + HM - er + c;
+      R[i] -= Ub[i];
+    });
     __syncthreads();
   } else {
     fine_pass1<HM, PA, PT, D>(Ub, T, eu, er);
@@ -312,21 +336,24 @@ __device__ __forceinline__ void fine_adjoint_level(float*& R, float*& Ub, float*
   { float* t = R; R = Ub; Ub = t; }
   if constexpr (J0 > 0) {
 #pragma unroll
-    for (int q = 0; q < NPF; ++q) {
-      const int i = threadIdx.x + q * kFineThreads;
-      if (i < sidn * sidn) {
-        const int r = i / sidn, c = i - r * sidn;
-        Ub[(HM - eun + r) * PA + HM - eun + c] = pf[q];
+    for (int k = 0; k < NR; ++k) {
+      const int r = wrp + NW * k;
+      float* drow = Ub + (HM - eun + r) * PA + HM - eun;
+#pragma unroll
+      for (int q = 0; q < NQ; ++q) {
+        const int c = lane + 32 * q;
+        if (r < sidn && c < sidn) drow[c] = pf[k][q];
       }
     }
     __syncthreads();
-    fine_adjoint_level<GEN, J1, J0 - 1>(R, Ub, T, a, n, J, l, ty0, tx0);
+    fine_adjoint_level<GEN, J1, J0 - 1, NTH>(R, Ub, T, a, n, J, l, ty0, tx0);
   }
 }
 
 // rin: r_{j1} per channel (class-permuted, stride 2^j1), channel stride rin_stride.
-template <int GEN, int J1>
-__global__ void __launch_bounds__(kFineThreads)
+// NTH threads: 1024 when the block's shared memory leaves room for one block per SM.
+template <int GEN, int J1, int NTH>
+__global__ void __launch_bounds__(NTH)
 k_fine_adjoint(int n, int J, const float* __restrict__ rin, size_t rin_stride, IuwtArgs a) {
   using G = FineGeo<GEN, J1>;
   constexpr int HM = G::HM, PA = G::PA;
@@ -340,11 +367,11 @@ k_fine_adjoint(int n, int J, const float* __restrict__ rin, size_t rin_stride, I
   load_region_class<HM, PA>(R, rin + (size_t)l * rin_stride, halo_r(J1), n, J1, ty0, tx0);
   load_region<HM, PA>(Ub, a.U + ((size_t)l * (J + 1) + J1 - 1) * P, halo_u(GEN, J1 - 1), n, ty0, tx0);
   __syncthreads();
-  fine_adjoint_level<GEN, J1, J1 - 1>(R, Ub, T, a, n, J, l, ty0, tx0);
+  fine_adjoint_level<GEN, J1, J1 - 1, NTH>(R, Ub, T, a, n, J, l, ty0, tx0);
   const int ci = int_col();
 #pragma unroll
-  for (int k = 0; k < 8; ++k) {
-    const int ri = int_row(k);
+  for (int k = 0; k < 4096 / NTH; ++k) {
+    const int ri = int_row<NTH>(k);
     a.S[(size_t)l * P + (size_t)(ty0 + ri) * n + tx0 + ci] = R[(HM + ri) * PA + HM + ci];
   }
 }
@@ -400,6 +427,18 @@ __device__ __forceinline__ void band_for(const CoarseGeo& g, F&& f) {
 // into registers before any store: a store between them would serialise the
 // loads, since local and remote shared pointers may alias.
 __device__ __forceinline__ void halo_exchange(cg::cluster_group& cl, float* X, int d, const CoarseGeo& g, int rank) {
+  if (g.RPC == g.M) {
+    // one block holds the whole sub-image: the halo rows are its own rows, wrapped
+    __syncthreads();
+    const int h2 = 2 * d, mm = g.M - 1, c = threadIdx.x & mm, step = blockDim.x >> g.lgM;
+    for (int hh = threadIdx.x >> g.lgM; hh < 2 * h2; hh += step) {
+      const int srow = (hh < h2 ? hh - h2 : g.M + hh - h2) & mm;
+      const int erow = hh < h2 ? g.HR - h2 + hh : g.HR + g.M + hh - h2;
+      X[erow * g.PA + c] = X[(g.HR + srow) * g.PA + c];
+    }
+    __syncthreads();
+    return;
+  }
   cl.sync();
   const int h2 = 2 * d, row0 = rank * g.RPC, mm = g.M - 1;
   const int c = threadIdx.x & mm, step = blockDim.x >> g.lgM, nrows = 2 * h2;
@@ -560,7 +599,7 @@ k_coarse_cl(int n, int J, int j1, int cs, const float* __restrict__ c_in, float*
     if constexpr (MODE == MODE_NORM) {
       const double tot = block_sum(acc, red);
       if (threadIdx.x == 0) partials[(size_t)blockIdx.y * gridDim.x + blockIdx.x] = tot;
-      cl.sync();
+      if (cs > 1) cl.sync();
       return;
     }
   } else {
@@ -603,7 +642,7 @@ k_coarse_cl(int n, int J, int j1, int cs, const float* __restrict__ c_in, float*
       band_for(g, [&](int r, int c) { dst[(r << g.lgM) + c] = src[r * PA + c]; });
     }
   }
-  cl.sync();   // no block leaves while a neighbour may still read its shared memory
+  if (cs > 1) cl.sync();   // no block leaves while a neighbour may still read its shared memory
 }
 
 // ================================================================== coarse levels, streaming fallback
@@ -726,7 +765,7 @@ __global__ void k_u0_pointwise(const float* __restrict__ D, float* __restrict__ 
 // ================================================================== host side
 size_t fine_smem_bytes(int gen, int j1, int adjoint) {
   const int hm = halo_max(gen, j1);
-  const size_t sd = kTile + 2 * hm, pa = sd + 1, ra = sd + kQ, pt = sd + kQ + 1, ni = (size_t)kTile * (kTile + 1);
+  const size_t sd = kTile + 2 * hm, pa = sd + 1, ra = sd, pt = sd + 1, ni = (size_t)kTile * (kTile + 1);
   const size_t na = ra * pa, nt = ra * pt;
   const size_t floats = adjoint ? 2 * na + nt : (gen == 1 ? na + nt + ni : 2 * na + nt + ni);
   return floats * sizeof(float);
@@ -794,13 +833,19 @@ cudaError_t launch_fine_analysis(const Geom& g, const IuwtArgs& a, int mode, cud
   return cudaErrorInvalidValue;
 }
 
+// The adjoint tile takes 1024 threads when its shared memory fits one block per SM only.
+static bool fine_adj_wide(int gen, int j1) { return fine_smem_bytes(gen, j1, 1) > 113 * 1024; }
+
 template <int GEN, int J1> static cudaError_t fine_adj(const Geom& g, const IuwtArgs& a, cudaStream_t s) {
   dim3 grid(g.n / kTile, g.n / kTile, g.L);
   const size_t P = (size_t)g.n * g.n;
   const bool from_u = (g.J == g.j1);
   const float* rin = from_u ? a.U + (size_t)g.J * P : a.rin;
   const size_t stride = from_u ? (size_t)(g.J + 1) * P : P;
-  k_fine_adjoint<GEN, J1><<<grid, kFineThreads, fine_smem_bytes(g, 1), s>>>(g.n, g.J, rin, stride, a);
+  if (fine_adj_wide(GEN, J1))
+    k_fine_adjoint<GEN, J1, 1024><<<grid, 1024, fine_smem_bytes(g, 1), s>>>(g.n, g.J, rin, stride, a);
+  else
+    k_fine_adjoint<GEN, J1, kFineThreads><<<grid, kFineThreads, fine_smem_bytes(g, 1), s>>>(g.n, g.J, rin, stride, a);
   return cudaGetLastError();
 }
 
@@ -896,11 +941,11 @@ template <int GEN> static cudaError_t cfg_gen(Geom& g) {
   if (g.J > 0 && g.j1 > 0) {
     switch (g.j1) {
       case 1: SET((k_fine_analysis<GEN, 1, 0>)) SET((k_fine_analysis<GEN, 1, 1>)) SET((k_fine_analysis<GEN, 1, 2>))
-              SET((k_fine_adjoint<GEN, 1>)) break;
+              SET((k_fine_adjoint<GEN, 1, 512>)) SET((k_fine_adjoint<GEN, 1, 1024>)) break;
       case 2: SET((k_fine_analysis<GEN, 2, 0>)) SET((k_fine_analysis<GEN, 2, 1>)) SET((k_fine_analysis<GEN, 2, 2>))
-              SET((k_fine_adjoint<GEN, 2>)) break;
+              SET((k_fine_adjoint<GEN, 2, 512>)) SET((k_fine_adjoint<GEN, 2, 1024>)) break;
       case 3: SET((k_fine_analysis<GEN, 3, 0>)) SET((k_fine_analysis<GEN, 3, 1>)) SET((k_fine_analysis<GEN, 3, 2>))
-              SET((k_fine_adjoint<GEN, 3>)) break;
+              SET((k_fine_adjoint<GEN, 3, 512>)) SET((k_fine_adjoint<GEN, 3, 1024>)) break;
     }
   }
   g.cs = 0;

@@ -6,6 +6,7 @@
 #include "internal.h"
 
 #include <cmath>
+#include <cstdlib>
 #include <cstdio>
 #include <cstring>
 #include <string>
@@ -115,7 +116,7 @@ Layout make_layout(const muffin_params* p) {
   Lo.pw = take((J + 4) * P * 4);
   size_t mp = 1024;
   mp = std::max(mp, (n / 64) * (n / 64) * L);
-  mp = std::max(mp, ((size_t)1 << (2 * Lo.j1)) * L);
+  mp = std::max(mp, (size_t)64 * 8 * L);   // coarse blocks for any split j1 <= 3 and cluster <= 8
   mp = std::max(mp, (P + 31) / 32);
   mp = std::max(mp, (n / 4) * L);
   mp = std::max(mp, (size_t)4096);
@@ -149,6 +150,8 @@ struct muffin_ctx {
   double mu_s, mu_l, tau, sigma, rho;
   double beta = 0, beta_closed = 0, ws_norm2 = 1, l_norm2 = 0;
   bool tau_auto = true;
+  bool split_auto = false;   // choose the wavelet split by timing at the first set_psf
+  bool tuned = false;
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t exec = nullptr;
   std::string err;
@@ -323,6 +326,70 @@ static void host_tables(const muffin_ctx* ctx, std::vector<char>& blob, const La
   put(lo.w, ctx->w.data(), ctx->w.size() * 8);
 }
 
+// Time one spatial half-pass (fine adjoint, fine analysis, coarse levels) of
+// the split in g on the context's buffers; milliseconds per pass.
+static int time_split(muffin_ctx* ctx, const Geom& g, float* ms) {
+  const Layout& lo = ctx->lo;
+  cudaStream_t s = ctx->stream;
+  IuwtArgs ia{};
+  ia.D = ctx->at<float>(lo.D);
+  ia.U = ctx->U();
+  ia.cr = ctx->at<float>(lo.cr);
+  ia.rin = ctx->at<float>(lo.cr);
+  ia.S = ctx->at<float>(lo.S);
+  ia.k = 0.25f;
+  ia.rho = 1.0f;
+  cudaEvent_t e0, e1;
+  CK(cudaEventCreate(&e0));
+  CK(cudaEventCreate(&e1));
+  const int reps = 3;
+  for (int it = 0; it < reps + 1; ++it) {
+    if (it == 1) CK(cudaEventRecord(e0, s));
+    if (g.j1 > 0) CK(launch_fine_adjoint(g, ia, s));
+    if (g.j1 > 0 || g.J == 0) CK(launch_fine_analysis(g, ia, MODE_UPDATE, s, nullptr));
+    if (g.J > g.j1)
+      CK(launch_coarse(g, g.j1 > 0 ? ia.cr : ia.D, g.j1 > 0 ? ia.cr : ia.S, ia.U, ia.k, ia.rho, MODE_UPDATE, nullptr, s,
+                       nullptr));
+  }
+  CK(cudaEventRecord(e1, s));
+  CK(cudaEventSynchronize(e1));
+  CK(cudaEventElapsedTime(ms, e0, e1));
+  *ms /= reps;
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  return MUFFIN_OK;
+}
+
+// Pick the fastest wavelet split for this cube by timing every valid one.  The
+// dual state is still zero at the first set_psf, so the class-permuted layout
+// of U may change; the planes the trials touch are cleared afterwards.
+static int autotune_split(muffin_ctx* ctx) {
+  const Geom base = ctx->g;
+  const int top = base.J < 3 ? base.J : 3;
+  float best = 0.0f;
+  Geom best_g = base;
+  bool any = false;
+  for (int j1 = 0; j1 <= top; ++j1) {
+    if (j1 > 0 && base.n < 64) continue;
+    if (!split_fits(base.n, base.J, base.gen, j1)) continue;
+    Geom g = base;
+    g.j1 = j1;
+    if (iuwt_configure(g) != cudaSuccess) { cudaGetLastError(); continue; }
+    float ms = 0.0f;
+    const int r = time_split(ctx, g, &ms);
+    if (r != MUFFIN_OK) return r;
+    if (!any || ms < best) { best = ms; best_g = g; any = true; }
+  }
+  if (any) ctx->g = best_g;
+  cudaError_t e = iuwt_configure(ctx->g);
+  if (e != cudaSuccess) return fail(ctx, MUFFIN_ERR_CUDA, "wavelet configuration", cudaGetErrorString(e));
+  const Layout& lo = ctx->lo;
+  CK(cudaMemsetAsync(ctx->U(), 0, (size_t)ctx->vox() * (ctx->g.J + 1) * 4, ctx->stream));
+  CK(cudaMemsetAsync(ctx->at<float>(lo.S), 0, ctx->vox() * 4, ctx->stream));
+  CK(cudaMemsetAsync(ctx->at<float>(lo.cr), 0, ctx->vox() * 4, ctx->stream));
+  return MUFFIN_OK;
+}
+
 // ----------------------------------------------------------------- C ABI
 extern "C" {
 
@@ -365,6 +432,7 @@ int muffin_init(muffin_ctx** out, const muffin_params* p, const float* d_dirty, 
   ctx->sigma = p->sigma > 0 ? p->sigma : 1.0;
   ctx->rho = p->rho > 0 ? p->rho : 1.0;
   ctx->tau_auto = !(p->tau > 0);
+  ctx->split_auto = p->fine_levels < 0 && p->nscales > 0 && getenv("MUFFIN_NO_AUTOTUNE") == nullptr;
   ctx->tau = p->tau > 0 ? p->tau : 0.0;
   if (ctx->p.power_iters <= 0) ctx->p.power_iters = 40;
   auto bail = [&](int code) { if (ctx->cap) cudaStreamDestroy(ctx->cap); g_init_error = ctx->err; delete ctx; return code; };
@@ -415,6 +483,11 @@ int muffin_set_psf(muffin_ctx* ctx, const float* d_psf) {
   CK(cudaMemcpyAsync(&h_cnt, cnt, sizeof(int), cudaMemcpyDeviceToHost, s));
   CK(cudaStreamSynchronize(s));
   if (h_cnt) return fail(ctx, MUFFIN_ERR_NONFINITE, "psf holds NaN or Inf");
+  if (ctx->split_auto && !ctx->tuned) {
+    const int r = autotune_split(ctx);
+    if (r != MUFFIN_OK) return r;
+    ctx->tuned = true;
+  }
   void* hh = ctx->ws + lo.hhat;
   void* yh = ctx->ws + lo.yhat;
   void* z = ctx->ws + lo.z64;

@@ -138,8 +138,9 @@ def test_checkpoint_resume_is_bitwise(lib):
     x, u, v, it = a.get_state()
     a.iterate(50)
     x_ref = a.get_cube().clone()
+    split = a.tiling()[0]
     a.close()
-    b = gpu_solver(cube, p)
+    b = gpu_solver(cube, p, fine_levels=split)   # same tiling: the split is chosen by timing otherwise
     b.set_state(x, u, v, it)
     b.iterate(50)
     x_b = b.get_cube()
@@ -162,6 +163,19 @@ def test_two_step_calibration(lib):
     s = mo.iterate(p0, mo.zero_state(p0), 30)
     s = mo.iterate(p1, s, 30)
     assert np.linalg.norm(gx - s.X) / np.linalg.norm(s.X) < 1e-4
+
+
+def test_autotuned_split_is_valid_and_reported(lib):
+    cube = small_cube(256, 4, 4, seed=36)
+    p = problem(cube, 4, 1, 0.25, 3.0)
+    m = gpu_solver(cube, p)
+    j1, cs = m.tiling()
+    m.iterate(3)
+    gx = to64(m.get_cube())
+    m.close()
+    assert 0 <= j1 <= 3 and cs in (0, 1, 2, 4, 8)
+    s = mo.iterate(p, mo.zero_state(p), 3)
+    assert np.linalg.norm(gx - s.X) / np.linalg.norm(s.X) < 1e-5
 
 
 def test_errors_are_reported(lib):
