@@ -39,6 +39,8 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-ttt", action="store_true")
+    ap.add_argument("--fine-levels", type=int, default=-1,
+                    help="wavelet split (levels on halo tiles); -1: chosen by timing at set-up")
     return ap.parse_args()
 
 
@@ -181,7 +183,7 @@ def main():
     cube = synth.make_cube(cfg, seed=cfg.seed + rank)
     L, n = cfg.nchan, cfg.n
     voxels = L * n * n
-    kw = dict(nscales=cfg.nscales, gen=1, mu_s=0.25, mu_l=3.0)
+    kw = dict(nscales=cfg.nscales, gen=1, mu_s=0.25, mu_l=3.0, fine_levels=args.fine_levels)
     m = Muffin(torch.from_numpy(cube.dirty).cuda(), torch.from_numpy(cube.psf).cuda(), **kw)
     stream = torch.cuda.current_stream()
 
