@@ -39,6 +39,7 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-ttt", action="store_true")
+    ap.add_argument("--no-batch", action="store_true")
     ap.add_argument("--fine-levels", type=int, default=-1,
                     help="wavelet split (levels on halo tiles); -1: chosen by timing at set-up")
     return ap.parse_args()
@@ -150,9 +151,8 @@ def reference_arm(args, rank: int) -> None:
 # ------------------------------------------------------------------ GPU arm
 def main():
     args = parse()
-    rank = int(os.environ.get("RANK", "0"))
-    world = int(os.environ.get("WORLD_SIZE", "1"))
-    local = int(os.environ.get("LOCAL_RANK", "0"))
+    from paper_1602_08847_gb300 import replicas
+    rank, world, local = replicas.world()
     if args.impl == "reference":
         reference_arm(args, rank)
         return
@@ -173,14 +173,10 @@ def main():
             dist.barrier()
 
     def max_over_ranks(v: float) -> float:
-        if not dist:
-            return v
-        t = torch.tensor([v], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        return float(t.item())
+        return replicas.max_over_ranks(v, dist, "cuda")
 
     cfg = synth.CONFIGS[args.config]
-    cube = synth.make_cube(cfg, seed=cfg.seed + rank)
+    cube = synth.make_cube(cfg, seed=replicas.rank_seed(cfg.seed, rank))
     L, n = cfg.nchan, cfg.n
     voxels = L * n * n
     kw = dict(nscales=cfg.nscales, gen=1, mu_s=0.25, mu_l=3.0, fine_levels=args.fine_levels)
@@ -200,7 +196,7 @@ def main():
     barrier()
     ms = max_over_ranks(e0.elapsed_time(e1))
     ms_step = ms / args.steps
-    value = voxels * world * args.steps / (ms / 1e3)
+    value = replicas.aggregate_throughput(voxels * args.steps, world, ms / 1e3)
     launches = m.kernels_per_iteration() * args.steps
     fine_levels, cluster = m.tiling()
 
@@ -261,6 +257,46 @@ def main():
                        "d2h_bytes_per_step": x.numel() * 4 / args.steps,
                        "what": f"muffin.solve(): H2D of y and PSF, set-up (FP64 spectra, power method), "
                                f"{args.steps} passes, D2H of X; one call"}
+
+    # four uneven cubes advanced together: one graph launch per pass (muffin_batch) vs one by one
+    if not args.no_batch and rank == 0:
+        from paper_1602_08847_gb300.muffin import Batch
+        ms = []
+        vox_c = 0
+        for name in ("C0", "C1", "C2", "C3"):
+            cc = synth.make_cube(name)
+            ms.append(Muffin(torch.from_numpy(cc.dirty).cuda(), torch.from_numpy(cc.psf).cuda(),
+                             nscales=cc.cfg.nscales, gen=1, mu_s=0.25, mu_l=3.0))
+            vox_c += cc.cfg.nchan * cc.cfg.n * cc.cfg.n
+        b = Batch(ms)
+        b.iterate(5)
+        torch.cuda.synchronize()
+        s0, s1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        s0.record()
+        b.iterate(args.steps)
+        s1.record()
+        torch.cuda.synchronize()
+        t_batch = s0.elapsed_time(s1) / args.steps
+        for m_ in ms:
+            m_.iterate(2)
+        torch.cuda.synchronize()
+        s0.record()
+        for _ in range(args.steps):
+            for m_ in ms:
+                m_.iterate(1)
+        s1.record()
+        torch.cuda.synchronize()
+        t_seq = s0.elapsed_time(s1) / args.steps
+        line["batched"] = {"workload": "128^2x16 + 256^2x32 + 512^2x64 + 1024^2x8, 40 sources, 60 antennas, J=4, "
+                                       "seeds 11-14, splits chosen per cube by the set-up autotuner",
+                           "voxels": vox_c, "ms_per_step": t_batch, "value": vox_c / (t_batch / 1e3),
+                           "unit": METRIC, "one_by_one_ms_per_step": t_seq,
+                           "tilings": [m_.tiling() for m_ in ms]}
+        b.close()
+        for m_ in ms:
+            m_.close()
+        del ms
+        torch.cuda.empty_cache()
 
     # plain method, time to 1e-4 relative objective on the 256x256x64 cube (F* from 2000 passes)
     if not args.no_ttt and rank == 0:

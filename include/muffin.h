@@ -137,6 +137,20 @@ int muffin_tiling(const muffin_ctx* ctx, int* fine_levels, int* cluster);
 
 const char* muffin_last_error(const muffin_ctx* ctx);  /* ctx may be NULL (init errors) */
 
+/* Batches of cubes of uneven sizes.  A batch captures one pass of Algorithm 1
+ * of every context (each with its own sizes, PSFs, tiling and workspace) as
+ * parallel branches of a single CUDA graph, so one graph launch per pass runs
+ * all cubes concurrently on the GPU.  The contexts must have had
+ * muffin_set_psf; they stay usable on their own.  Work is enqueued on stream:
+ * order it with the contexts' own streams (use the same stream, or
+ * synchronise).  A context changed after the batch was built (muffin_set_mu,
+ * muffin_set_psf) is picked up by a new capture at the next iterate. */
+typedef struct muffin_batch muffin_batch;
+int muffin_batch_create(muffin_batch** batch, muffin_ctx* const* ctxs, int n, cudaStream_t stream);
+int muffin_batch_iterate(muffin_batch* batch, int n_iter);
+const char* muffin_batch_last_error(const muffin_batch* batch);  /* batch may be NULL (create errors) */
+void muffin_batch_destroy(muffin_batch* batch);
+
 /* Spectral l1 sum  sum_n ||W_lambda x^n||_1  of a device cube d_x [nchan][n_pix]
  * (float32, channel-major), written as one double to d_out (device), for
  * callers that cannot allocate device memory at all: code inside a host

@@ -154,6 +154,7 @@ struct muffin_ctx {
   bool tuned = false;
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t exec = nullptr;
+  unsigned version = 0;    // bumped whenever the pass changes (step sizes, weights, tiling)
   std::string err;
 
   template <typename T> T* at(size_t off) const { return reinterpret_cast<T*>(ws + off); }
@@ -186,6 +187,7 @@ static void drop_graph(muffin_ctx* ctx) {
   if (ctx->graph) cudaGraphDestroy(ctx->graph);
   ctx->exec = nullptr;
   ctx->graph = nullptr;
+  ++ctx->version;
 }
 
 static void compute_steps(muffin_ctx* ctx) {
@@ -765,6 +767,126 @@ void muffin_destroy(muffin_ctx* ctx) {
   drop_graph(ctx);
   if (ctx->cap) cudaStreamDestroy(ctx->cap);
   delete ctx;
+}
+
+}  // extern "C"
+
+// ----------------------------------------------------------------- batches of cubes
+struct muffin_batch {
+  std::vector<muffin_ctx*> ctx;
+  std::vector<unsigned> version;
+  std::vector<cudaStream_t> side;
+  std::vector<cudaEvent_t> done;
+  cudaStream_t stream = nullptr, cap = nullptr;
+  cudaEvent_t fork = nullptr;
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  std::string err;
+};
+
+static int bfail(muffin_batch* b, int code, const char* what, const char* detail = nullptr) {
+  std::string m = what;
+  if (detail) { m += ": "; m += detail; }
+  if (b) b->err = m; else g_init_error = m;
+  return code;
+}
+
+#define BCK(call)                                                                        \
+  do {                                                                                   \
+    cudaError_t e_ = (call);                                                             \
+    if (e_ != cudaSuccess) return bfail(b, MUFFIN_ERR_CUDA, #call, cudaGetErrorString(e_)); \
+  } while (0)
+
+static void batch_drop_graph(muffin_batch* b) {
+  if (b->exec) cudaGraphExecDestroy(b->exec);
+  if (b->graph) cudaGraphDestroy(b->graph);
+  b->exec = nullptr;
+  b->graph = nullptr;
+}
+
+// One pass of every cube as parallel branches of one graph.
+static int batch_capture(muffin_batch* b) {
+  batch_drop_graph(b);
+  BCK(cudaStreamBeginCapture(b->cap, cudaStreamCaptureModeThreadLocal));
+  int r = MUFFIN_OK;
+  std::string why;
+  cudaError_t e = cudaEventRecord(b->fork, b->cap);
+  for (size_t i = 0; i < b->ctx.size() && e == cudaSuccess && r == MUFFIN_OK; ++i) {
+    e = cudaStreamWaitEvent(b->side[i], b->fork, 0);
+    if (e == cudaSuccess) r = enqueue_pass(b->ctx[i], b->side[i], nullptr);
+    if (r != MUFFIN_OK) why = b->ctx[i]->err;
+    if (e == cudaSuccess && r == MUFFIN_OK) e = cudaEventRecord(b->done[i], b->side[i]);
+    if (e == cudaSuccess && r == MUFFIN_OK) e = cudaStreamWaitEvent(b->cap, b->done[i], 0);
+  }
+  cudaGraph_t gr = nullptr;
+  const cudaError_t e2 = cudaStreamEndCapture(b->cap, &gr);
+  if (r != MUFFIN_OK || e != cudaSuccess || e2 != cudaSuccess) {
+    if (gr) cudaGraphDestroy(gr);
+    if (r != MUFFIN_OK) return bfail(b, r, "capture of a cube's pass", why.c_str());
+    return bfail(b, MUFFIN_ERR_CUDA, "batch capture", cudaGetErrorString(e != cudaSuccess ? e : e2));
+  }
+  b->graph = gr;
+  BCK(cudaGraphInstantiate(&b->exec, b->graph, 0));
+  for (size_t i = 0; i < b->ctx.size(); ++i) b->version[i] = b->ctx[i]->version;
+  return MUFFIN_OK;
+}
+
+extern "C" {
+
+int muffin_batch_create(muffin_batch** out, muffin_ctx* const* ctxs, int n, cudaStream_t stream) {
+  if (!out || !ctxs || n < 1) return bfail(nullptr, MUFFIN_ERR_ARG, "batch needs an out-pointer and n >= 1 contexts");
+  *out = nullptr;
+  for (int i = 0; i < n; ++i) {
+    if (!ctxs[i]) return bfail(nullptr, MUFFIN_ERR_ARG, "NULL context in batch");
+    if (ctxs[i]->state < 1) return bfail(nullptr, MUFFIN_ERR_STATE, "every context of a batch needs muffin_set_psf first");
+    for (int k = 0; k < i; ++k)
+      if (ctxs[k] == ctxs[i]) return bfail(nullptr, MUFFIN_ERR_ARG, "a context appears twice in the batch");
+  }
+  muffin_batch* b = new muffin_batch();
+  b->stream = stream;
+  b->ctx.assign(ctxs, ctxs + n);
+  b->version.assign(n, ~0u);
+  b->side.assign(n, nullptr);
+  b->done.assign(n, nullptr);
+  cudaError_t e = cudaStreamCreateWithFlags(&b->cap, cudaStreamNonBlocking);
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->fork, cudaEventDisableTiming);
+  for (int i = 0; i < n && e == cudaSuccess; ++i) {
+    e = cudaStreamCreateWithFlags(&b->side[i], cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->done[i], cudaEventDisableTiming);
+  }
+  if (e != cudaSuccess) {
+    muffin_batch_destroy(b);
+    return bfail(nullptr, MUFFIN_ERR_CUDA, "batch streams", cudaGetErrorString(e));
+  }
+  *out = b;
+  return MUFFIN_OK;
+}
+
+int muffin_batch_iterate(muffin_batch* b, int n_iter) {
+  if (!b) return bfail(nullptr, MUFFIN_ERR_ARG, "batch is NULL");
+  if (n_iter < 0) return bfail(b, MUFFIN_ERR_ARG, "n_iter < 0");
+  if (n_iter == 0) return MUFFIN_OK;
+  bool stale = !b->exec;
+  for (size_t i = 0; i < b->ctx.size(); ++i) stale = stale || b->version[i] != b->ctx[i]->version;
+  if (stale) {
+    const int r = batch_capture(b);
+    if (r != MUFFIN_OK) return r;
+  }
+  for (int i = 0; i < n_iter; ++i) BCK(cudaGraphLaunch(b->exec, b->stream));
+  for (muffin_ctx* c : b->ctx) c->iter += n_iter;
+  return MUFFIN_OK;
+}
+
+const char* muffin_batch_last_error(const muffin_batch* b) { return b ? b->err.c_str() : g_init_error.c_str(); }
+
+void muffin_batch_destroy(muffin_batch* b) {
+  if (!b) return;
+  batch_drop_graph(b);
+  for (cudaStream_t s : b->side) if (s) cudaStreamDestroy(s);
+  for (cudaEvent_t e : b->done) if (e) cudaEventDestroy(e);
+  if (b->fork) cudaEventDestroy(b->fork);
+  if (b->cap) cudaStreamDestroy(b->cap);
+  delete b;
 }
 
 }  // extern "C"

@@ -62,6 +62,10 @@ def _load():
         "muffin_kernels_per_iteration": (I, [P]),
         "muffin_tiling": (I, [P, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int)]),
         "muffin_last_error": (ctypes.c_char_p, [P]),
+        "muffin_batch_create": (I, [ctypes.POINTER(P), ctypes.POINTER(P), I, P]),
+        "muffin_batch_iterate": (I, [P, I]),
+        "muffin_batch_last_error": (ctypes.c_char_p, [P]),
+        "muffin_batch_destroy": (V, [P]),
         "muffin_destroy": (V, [P]),
     }
     for name, (res, args) in sig.items():
@@ -219,6 +223,36 @@ class Muffin:
             torch.cuda.current_stream().synchronize()
             _lib.muffin_destroy(self._ctx)
             self._ctx = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Batch:
+    """Several Muffin problems (cubes of any sizes) advanced together: one CUDA
+    graph launch per pass runs every cube's kernels as parallel branches."""
+
+    def __init__(self, problems: list):
+        self.problems = list(problems)
+        arr = (ctypes.c_void_p * len(self.problems))(*[m.ctx.value for m in self.problems])
+        self._b = ctypes.c_void_p()
+        r = _lib.muffin_batch_create(ctypes.byref(self._b), arr, len(self.problems), _stream())
+        if r != MUFFIN_OK:
+            raise MuffinError(r, _lib.muffin_batch_last_error(None).decode())
+
+    def iterate(self, n: int = 1):
+        r = _lib.muffin_batch_iterate(self._b, int(n))
+        if r != MUFFIN_OK:
+            raise MuffinError(r, _lib.muffin_batch_last_error(self._b).decode())
+
+    def close(self):
+        if getattr(self, "_b", None) and self._b.value:
+            torch.cuda.current_stream().synchronize()
+            _lib.muffin_batch_destroy(self._b)
+            self._b = ctypes.c_void_p()
 
     def __del__(self):
         try:
