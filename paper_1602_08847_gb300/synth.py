@@ -160,3 +160,35 @@ def random_state(shape_x: tuple, nscales: int, seed: int, scale: float = 1.0):
 def random_field(shape: tuple, seed: int, lo: float = -1.0, hi: float = 1.0) -> np.ndarray:
     rng = np.random.Generator(np.random.PCG64(seed))
     return rng.uniform(lo, hi, shape)
+
+
+# --------------------------------------------------------------------------
+# inputs of the warm-start network
+# --------------------------------------------------------------------------
+
+# (input features, output features) of the six 3x3x3 layers.
+NET_LAYERS = ((1, 32), (32, 32), (32, 32), (32, 32), (32, 32), (32, 1))
+
+
+def bf16_round(a) -> np.ndarray:
+    """float32 copy of ``a`` rounded to the nearest bfloat16 (ties to even),
+    so that a bfloat16 consumer and a float64 checker see the same numbers."""
+    u = np.ascontiguousarray(a, dtype=np.float32).view(np.uint32).astype(np.uint64)
+    u = (u + 0x7FFF + ((u >> 16) & 1)) & 0xFFFF0000
+    return u.astype(np.uint32).view(np.float32)
+
+
+def net_init(seed: int, bf16: bool = True) -> np.ndarray:
+    """Seeded initial parameters of the network, packed layer by layer as
+    weights [co][ci][3][3][3] then biases [co]: He-normal weights
+    (std sqrt(2 / (27 ci))), zero biases; the last layer is scaled down by 10 so
+    the first predictions are small."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    parts = []
+    for k, (ci, co) in enumerate(NET_LAYERS):
+        w = rng.standard_normal(co * ci * 27) * np.sqrt(2.0 / (27 * ci))
+        if k == len(NET_LAYERS) - 1:
+            w *= 0.1
+        parts += [w, np.zeros(co)]
+    theta = np.concatenate(parts).astype(np.float32)
+    return bf16_round(theta) if bf16 else theta

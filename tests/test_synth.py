@@ -48,3 +48,23 @@ def test_point_sources_fraction():
     cube = small(n_src=40, point_frac=1.0, n=64)
     # all-delta sky: every non-zero pixel of a channel is an isolated source pixel
     assert np.count_nonzero(cube.sky[0]) <= 40
+
+
+def test_bf16_round_is_nearest_even_on_the_bfloat16_grid():
+    from paper_1602_08847_gb300 import synth
+    x = np.array([1.0, 1.0 + 2.0 ** -8, 1.0 + 3 * 2.0 ** -8, 1.0 + 2.0 ** -9, -3.140625, 1e-30], dtype=np.float32)
+    r = synth.bf16_round(x)
+    assert r[0] == 1.0
+    assert r[1] == 1.0                          # tie -> even mantissa
+    assert r[2] == np.float32(1.0 + 4 * 2.0 ** -8)   # tie -> even (rounds up)
+    assert r[3] == 1.0
+    assert r[4] == np.float32(-3.140625)        # already on the grid
+    assert (r.view(np.uint32) & 0xFFFF == 0).all()
+
+
+def test_net_init_sizes():
+    from paper_1602_08847_gb300 import synth
+    from oracle import warmstart_net as wn
+    theta = synth.net_init(0)
+    assert theta.size == wn.n_params() == 112481
+    assert np.array_equal(theta, synth.bf16_round(theta))
