@@ -1,0 +1,119 @@
+/*
+ * libmuffin warm-start network -- a small 3D convolutional network that
+ * predicts, from a dirty cube, a starting cube for Algorithm 1.
+ *
+ * The paper's own warm start is the two-step schedule of Sec. 4: the second
+ * run of Algorithm 1 starts from the cube the first run produced.  This
+ * network generalises that: trained on (dirty cube, cube after a number of
+ * passes of Algorithm 1) pairs, its prediction becomes X of the first pass
+ * (muffin_set_cube), and Algorithm 1 runs on from there.  The paper has no
+ * network; everything below is defined here.
+ *
+ * Network: six zero-padded 3x3x3 cross-correlations over (channel, row,
+ * column) of the cube, 1 -> 32 -> 32 -> 32 -> 32 -> 32 -> 1 feature maps, a
+ * bias and a ReLU after each layer but the last.  Input a0 = y / s with
+ * s = max |y| over the dirty cube; prediction max(s * z6, 0).  Loss: mean
+ * over voxels of (z6 - t / s)^2 for a target cube t.  Training: Adam (Kingma
+ * and Ba, ICLR 2015, Algorithm 1; beta1 0.9, beta2 0.999, eps 1e-8).
+ *
+ * Arithmetic: weights, activations and activation gradients are bfloat16,
+ * every sum is accumulated in float32; master weights, their gradients and
+ * Adam's moments are float32.  The 32 -> 32 layers and their gradients run on
+ * the tensor cores.
+ *
+ * Parameters travel as one packed float32 vector: for each layer in order,
+ * its weights [co][ci][3][3][3] (tap index (dz+1)*9 + (dy+1)*3 + (dx+1) for
+ * the offset (dz, dy, dx) along (channel, row, column)) and then its biases
+ * [co]; 112481 values in all.
+ *
+ * Cubes: float32 [nz][ny][nx] (nz = spectral channels).  Feature maps:
+ * bfloat16 [nz][ny][nx][32] (features innermost), passed as void pointers to
+ * 16-bit storage.  Pointers named d_* are device pointers, h_* host pointers;
+ * the library never allocates: the caller provides workspaces.  Work goes on
+ * the stream given at creation.  Every call returns a muffin_status
+ * (include/muffin.h); muffin_net_last_error describes the last failure.
+ */
+#ifndef MUFFIN_NET_H
+#define MUFFIN_NET_H
+
+#include <stddef.h>
+#include <cuda_runtime_api.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct muffin_net muffin_net;
+
+/* Number of packed float32 parameters (112481). */
+int muffin_net_num_params(void);
+
+/* Device workspace for a network working on nz x ny x nx cubes; training != 0
+ * also holds every activation, the gradients and Adam's moments.  0 if the
+ * sizes are invalid (each >= 1, nz*ny*nx < 2^31 / 32). */
+size_t muffin_net_workspace_bytes(int nz, int ny, int nx, int training);
+
+/* Create a network context over a caller-owned workspace (>= the bytes
+ * above, 256-byte aligned, valid until muffin_net_destroy).  The parameters
+ * start at zero: call muffin_net_set_params. */
+int muffin_net_create(muffin_net** net, int nz, int ny, int nx, int training, void* d_workspace,
+                      size_t ws_bytes, cudaStream_t stream);
+
+/* Load packed float32 parameters (device, 112481 values); resets Adam's
+ * moments and step count.  Asynchronous. */
+int muffin_net_set_params(muffin_net* net, const float* d_theta);
+/* Copy the current packed parameters out (device).  Asynchronous. */
+int muffin_net_get_params(const muffin_net* net, float* d_theta);
+
+/* Prediction of the starting cube: d_x = max(s * net(d_dirty / s), 0), both
+ * float32 [nz][ny][nx] on the device.  Asynchronous. */
+int muffin_net_predict(muffin_net* net, const float* d_dirty, float* d_x);
+
+/* Loss at (d_dirty, d_target) and its packed gradient (device float32,
+ * 112481 values), without changing the parameters.  Training contexts only.
+ * h_loss (may be NULL) receives the loss; if given, the call synchronises. */
+int muffin_net_loss_grad(muffin_net* net, const float* d_dirty, const float* d_target, float* d_grad,
+                         double* h_loss);
+
+/* One Adam step on the pair (d_dirty, d_target) at learning rate lr.
+ * Training contexts only.  d_loss (device, may be NULL) receives the loss of
+ * the pair before the step, as a double.  Asynchronous. */
+int muffin_net_train_step(muffin_net* net, const float* d_dirty, const float* d_target, float lr,
+                          double* d_loss);
+
+const char* muffin_net_last_error(const muffin_net* net);  /* net may be NULL (create errors) */
+void muffin_net_destroy(muffin_net* net);
+
+/* ---- single layers (the kernels the network is made of), for callers that
+ * compose their own networks and for checking each kernel on its own ----
+ * A 32 -> 32 layer on a [nz][ny][nx][32] bfloat16 map.  d_w: float32 weights
+ * [32][32][3][3][3] as in the packed vector (rounded to bfloat16 inside).
+ * d_scratch: device, >= muffin_conv3d_scratch_bytes(nz, ny, nx) bytes. */
+size_t muffin_conv3d_scratch_bytes(int nz, int ny, int nx);
+
+/* d_z = act(conv(d_a, W) + b): act = ReLU if relu != 0; d_b may be NULL
+ * (no bias).  Output bfloat16 [nz][ny][nx][32]. */
+int muffin_conv3d_forward(const void* d_a, const float* d_w, const float* d_b, int relu, void* d_z,
+                          int nz, int ny, int nx, void* d_scratch, size_t scratch_bytes, cudaStream_t stream);
+
+/* Gradient with respect to the layer input: d_da = m * conv^T(d_dz, W), where
+ * m = (d_mask > 0) elementwise if d_mask != NULL (the ReLU of the previous
+ * layer, given by its output), else 1.  All maps bfloat16 [nz][ny][nx][32]. */
+int muffin_conv3d_backward_data(const void* d_dz, const float* d_w, const void* d_mask, void* d_da,
+                                int nz, int ny, int nx, void* d_scratch, size_t scratch_bytes,
+                                cudaStream_t stream);
+
+/* Gradients with respect to the weights (d_dw, float32 [32][32][3][3][3])
+ * and the biases (d_db, float32 [32], may be NULL) of a layer with input d_a
+ * and output gradient d_dz (both bfloat16 [nz][ny][nx][32]). */
+int muffin_conv3d_backward_weights(const void* d_a, const void* d_dz, float* d_dw, float* d_db,
+                                   int nz, int ny, int nx, void* d_scratch, size_t scratch_bytes,
+                                   cudaStream_t stream);
+
+/* Description of the last failed single-layer call (process-wide). */
+const char* muffin_conv3d_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* MUFFIN_NET_H */

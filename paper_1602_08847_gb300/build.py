@@ -1,6 +1,7 @@
 """Build libmuffin.so (the CUDA library behind the C ABI in include/muffin.h).
 
-Each translation unit under csrc/ is compiled for sm_103a in parallel, then
+Each translation unit under csrc/ (the MUFFIN pass and the warm-start
+network) is compiled for sm_103a in parallel, then
 linked into paper_1602_08847_gb300/libmuffin.so.  Objects go to _build/ at the
 repository root.  Usage: ``python -m paper_1602_08847_gb300.build``.
 """
@@ -20,7 +21,7 @@ BUILD = os.path.join(ROOT, "_build")
 LIB = os.path.join(PKG, "libmuffin.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I", INCLUDE, "-I", CSRC]
-SOURCES = ["k_fft.cu", "k_iuwt.cu", "k_spectral.cu", "k_misc.cu", "muffin.cu", "k_noalloc.cu"]
+SOURCES = ["k_fft.cu", "k_iuwt.cu", "k_spectral.cu", "k_misc.cu", "muffin.cu", "k_noalloc.cu", "k_net.cu"]
 
 
 def nvcc() -> str:

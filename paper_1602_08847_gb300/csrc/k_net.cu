@@ -1,0 +1,1130 @@
+// Warm-start network: six zero-padded 3x3x3 convolution layers over the
+// cube (1 -> 32 -> 32 -> 32 -> 32 -> 32 -> 1 feature maps), its loss, its
+// gradients and Adam, all in bfloat16 with float32 accumulation.
+//
+// Feature maps are [nz][ny][nx][32] bfloat16 (64 bytes per voxel).  Every
+// kernel works on output tiles of 2 x 8 x 16 voxels (channel, row, column)
+// whose inputs, with a one-voxel halo (4 x 10 x 18), are staged in shared
+// memory by cp.async with zero fill outside the cube (the zero padding of the
+// layers).  In shared memory a voxel's 64 bytes are four 16-byte chunks, chunk
+// c of row r stored at chunk c ^ ((r >> 1) & 3): eight consecutive rows read
+// at the same chunk then hit eight different bank groups, which keeps the
+// ldmatrix loads below free of conflicts.
+//
+// The 32 -> 32 layers are implicit GEMMs on the tensor cores
+// (mma.m16n8k16, bfloat16 in, float32 accumulate):
+//   forward      z[p][co]  = sum_tap sum_ci a[p + d(tap)][ci] W[tap][co][ci]
+//                 (M = voxels, N = co, K = 27 taps x 32 ci),
+//   input grad   da[p][ci] = sum_tap sum_co dz[p - d(tap)][co] W[tap][co][ci],
+//                 the same kernel on the flipped, transposed weights,
+//   weight grad  dW[tap][co][ci] = sum_p dz[p][co] a[p + d(tap)][ci]
+//                 (M = co, N = ci, K = voxels), one warp per tap.
+// The 1 -> 32 and 32 -> 1 layers are 27 or 864 multiply-adds per voxel and
+// output; they run on the CUDA cores.  Every reduction over voxels is a
+// per-block partial sum followed by a fixed-order sum: results do not depend
+// on scheduling.
+#include <cuda_runtime.h>
+#include <cuda_bf16.h>
+#include <stdint.h>
+
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+
+#include "device.cuh"
+#include "muffin.h"
+#include "muffin_net.h"
+
+namespace mnet {
+
+using bf16 = __nv_bfloat16;
+using bf162 = __nv_bfloat162;
+
+constexpr int C = 32;                        // features of the hidden layers
+constexpr int NTAP = 27;
+constexpr int TZ = 2, TY = 8, TX = 16;       // output tile (channel, row, column)
+constexpr int TV = TZ * TY * TX;             // 256 voxels
+constexpr int HZ = TZ + 2, HY = TY + 2, HX = TX + 2;
+constexpr int HV = HZ * HY * HX;             // 720 voxels with halo
+constexpr int ROWB = C * 2;                  // 64 bytes per voxel of a map
+constexpr int WMID = NTAP * C * C;           // 27648 weights of a 32 -> 32 layer
+constexpr int NLAYER = 6;
+constexpr int kCi[NLAYER] = {1, 32, 32, 32, 32, 32};
+constexpr int kCo[NLAYER] = {32, 32, 32, 32, 32, 1};
+constexpr int kMaxPart = 512;                // cap of per-block partial slots (weight gradients)
+constexpr int kMaxLossPart = 1024;
+
+constexpr int conv_smem = NTAP * C * ROWB + HV * ROWB;      // 55296 + 46080
+constexpr int last_smem = HV * ROWB + NTAP * C * 4;         // 46080 + 3456
+
+struct Dims {
+  int nz, ny, nx;
+  int tx, ty, tz;   // tiles along each axis
+  int ntiles;
+  long long nvox;
+};
+
+inline Dims make_dims(int nz, int ny, int nx) {
+  Dims d;
+  d.nz = nz; d.ny = ny; d.nx = nx;
+  d.tx = (nx + TX - 1) / TX; d.ty = (ny + TY - 1) / TY; d.tz = (nz + TZ - 1) / TZ;
+  d.ntiles = d.tx * d.ty * d.tz;
+  d.nvox = (long long)nz * ny * nx;
+  return d;
+}
+
+// ------------------------------------------------------------------ helpers
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ uint32_t swz(int row, int chunk) {
+  return (uint32_t)(row * ROWB + ((chunk ^ ((row >> 1) & 3)) << 4));
+}
+
+__device__ __forceinline__ void cp_async16(uint32_t dst, const void* src, int src_bytes) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(dst), "l"(src), "r"(src_bytes) : "memory");
+}
+
+__device__ __forceinline__ void cp_async_wait_all() {
+  asm volatile("cp.async.commit_group;\ncp.async.wait_group 0;\n" ::: "memory");
+}
+
+__device__ __forceinline__ void ldsm_x4(uint32_t addr, uint32_t& r0, uint32_t& r1, uint32_t& r2, uint32_t& r3) {
+  asm volatile("ldmatrix.sync.aligned.m8n8.x4.shared.b16 {%0,%1,%2,%3}, [%4];\n"
+               : "=r"(r0), "=r"(r1), "=r"(r2), "=r"(r3) : "r"(addr));
+}
+
+__device__ __forceinline__ void ldsm_x4_t(uint32_t addr, uint32_t& r0, uint32_t& r1, uint32_t& r2, uint32_t& r3) {
+  asm volatile("ldmatrix.sync.aligned.m8n8.x4.trans.shared.b16 {%0,%1,%2,%3}, [%4];\n"
+               : "=r"(r0), "=r"(r1), "=r"(r2), "=r"(r3) : "r"(addr));
+}
+
+// D += A (16x16, row) * B (16x8, col), bfloat16 in, float32 accumulate.
+__device__ __forceinline__ void mma_bf16(float* d, const uint32_t* a, uint32_t b0, uint32_t b1) {
+  asm volatile(
+      "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+      "{%0,%1,%2,%3};\n"
+      : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+      : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
+}
+
+__device__ __forceinline__ void tile_origin(int tile, const Dims& d, int& z0, int& y0, int& x0) {
+  const int tx = tile % d.tx;
+  const int r = tile / d.tx;
+  x0 = tx * TX;
+  y0 = (r % d.ty) * TY;
+  z0 = (r / d.ty) * TZ;
+}
+
+__device__ __forceinline__ bool inside(const Dims& d, int z, int y, int x) {
+  return (unsigned)z < (unsigned)d.nz && (unsigned)y < (unsigned)d.ny && (unsigned)x < (unsigned)d.nx;
+}
+
+__device__ __forceinline__ size_t vox(const Dims& d, int z, int y, int x) {
+  return ((size_t)z * d.ny + y) * d.nx + x;
+}
+
+// NZS slices of a map starting at channel zs, rows y0-1 .. y0+TY, columns
+// x0-1 .. x0+TX, into swizzled shared rows h = (hz*HY + hy)*HX + hx.
+template <int NZS>
+__device__ __forceinline__ void load_map_halo(uint32_t s, const bf16* __restrict__ g, const Dims& d, int zs, int y0,
+                                              int x0) {
+  constexpr int N = NZS * HY * HX * 4;
+  for (int i = threadIdx.x; i < N; i += blockDim.x) {
+    const int c = i & 3, h = i >> 2;
+    const int hx = h % HX, t = h / HX, hy = t % HY, hz = t / HY;
+    const int gz = zs + hz, gy = y0 - 1 + hy, gx = x0 - 1 + hx;
+    const bool ok = inside(d, gz, gy, gx);
+    const bf16* src = ok ? g + vox(d, gz, gy, gx) * C + c * 8 : g;
+    cp_async16(s + swz(h, c), src, ok ? 16 : 0);
+  }
+}
+
+// The tile's own TV voxels of a map, row r = (tz*TY + ty)*TX + tx.
+__device__ __forceinline__ void load_map_tile(uint32_t s, const bf16* __restrict__ g, const Dims& d, int z0, int y0,
+                                              int x0) {
+  for (int i = threadIdx.x; i < TV * 4; i += blockDim.x) {
+    const int c = i & 3, r = i >> 2;
+    const int gz = z0 + (r >> 7), gy = y0 + ((r >> 4) & 7), gx = x0 + (r & 15);
+    const bool ok = inside(d, gz, gy, gx);
+    const bf16* src = ok ? g + vox(d, gz, gy, gx) * C + c * 8 : g;
+    cp_async16(s + swz(r, c), src, ok ? 16 : 0);
+  }
+}
+
+// Scalar field halo (float32 cube or bfloat16 single-feature map) into s[h], zero outside.
+template <typename T>
+__device__ __forceinline__ void load_scalar_halo(float* s, const T* __restrict__ g, const Dims& d, int z0, int y0,
+                                                 int x0) {
+  for (int h = threadIdx.x; h < HV; h += blockDim.x) {
+    const int hx = h % HX, t = h / HX, hy = t % HY, hz = t / HY;
+    const int gz = z0 - 1 + hz, gy = y0 - 1 + hy, gx = x0 - 1 + hx;
+    float v = 0.f;
+    if (inside(d, gz, gy, gx)) v = static_cast<float>(g[vox(d, gz, gy, gx)]);
+    s[h] = v;
+  }
+}
+
+__device__ __forceinline__ void unpack8(uint4 q, float* f) {
+  const bf162* p = reinterpret_cast<const bf162*>(&q);
+#pragma unroll
+  for (int e = 0; e < 4; ++e) {
+    const float2 t = __bfloat1622float2(p[e]);
+    f[2 * e] = t.x;
+    f[2 * e + 1] = t.y;
+  }
+}
+
+__device__ __forceinline__ uint4 pack8(const float* f) {
+  uint4 q;
+  bf162* p = reinterpret_cast<bf162*>(&q);
+#pragma unroll
+  for (int e = 0; e < 4; ++e) p[e] = __floats2bfloat162_rn(f[2 * e], f[2 * e + 1]);
+  return q;
+}
+
+// ------------------------------------------------------------------ 32 -> 32 layers on the tensor cores
+
+enum { EPI_RELU = 0, EPI_BIAS = 1, EPI_MASK = 2 };
+
+// out = epilogue(sum_tap sum_k in[p + d(tap)][k] wk[tap][n][k]); wk rows n hold
+// the 32 reduction features contiguously.  EPI_RELU / EPI_BIAS add bias[n]
+// (bias may be null) and EPI_RELU clamps at 0; EPI_MASK zeroes outputs whose
+// mask entry is not > 0 (mask may be null).  Persistent: each block loads the
+// weights once and walks tiles with stride gridDim.x.  8 warps; warp w owns
+// output rows 2w and 2w+1 of the tile (16 voxels each).
+template <int EPI>
+__global__ void __launch_bounds__(256, 2)
+k_conv_tc(const bf16* __restrict__ in, const bf16* __restrict__ wk, const float* __restrict__ bias,
+          const bf16* __restrict__ mask, bf16* __restrict__ out, Dims d) {
+  extern __shared__ __align__(128) unsigned char smem[];
+  const uint32_t s_w = smem_u32(smem);
+  const uint32_t s_a = s_w + NTAP * C * ROWB;
+  for (int i = threadIdx.x; i < NTAP * C * 4; i += blockDim.x) {
+    const int rr = i >> 2, c = i & 3;
+    cp_async16(s_w + swz(rr, c), wk + rr * C + c * 8, 16);
+  }
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int g = lane >> 2, tq = lane & 3;
+  const int a_vox = (lane & 7) + ((lane >> 3) & 1) * 8;   // ldmatrix row of the A strip
+  const int a_chk = lane >> 4;
+  const int b_row = (lane & 7) + ((lane >> 4) << 3);      // weight row within a pair of n-tiles
+  const int b_chk = (lane >> 3) & 1;
+  float bn[4][2];
+#pragma unroll
+  for (int nt = 0; nt < 4; ++nt) {
+    const int n = nt * 8 + tq * 2;
+    bn[nt][0] = (EPI != EPI_MASK && bias) ? bias[n] : 0.f;
+    bn[nt][1] = (EPI != EPI_MASK && bias) ? bias[n + 1] : 0.f;
+  }
+
+  for (int tile = blockIdx.x; tile < d.ntiles; tile += gridDim.x) {
+    int z0, y0, x0;
+    tile_origin(tile, d, z0, y0, x0);
+    __syncthreads();                       // the previous tile's reads are done
+    load_map_halo<HZ>(s_a, in, d, z0 - 1, y0, x0);
+    cp_async_wait_all();
+    __syncthreads();
+
+    float acc[2][4][4];
+#pragma unroll
+    for (int r = 0; r < 2; ++r)
+#pragma unroll
+      for (int nt = 0; nt < 4; ++nt)
+#pragma unroll
+        for (int e = 0; e < 4; ++e) acc[r][nt][e] = 0.f;
+
+    const int row0 = warp * 2;
+#pragma unroll 1
+    for (int t = 0; t < NTAP; ++t) {
+      const int kz = t / 9, ky = (t / 3) % 3, kx = t % 3;
+#pragma unroll
+      for (int kc = 0; kc < 2; ++kc) {
+        uint32_t b[4][2];
+#pragma unroll
+        for (int p = 0; p < 2; ++p)
+          ldsm_x4(s_w + swz(t * C + p * 16 + b_row, kc * 2 + b_chk), b[2 * p][0], b[2 * p][1], b[2 * p + 1][0],
+                  b[2 * p + 1][1]);
+#pragma unroll
+        for (int r = 0; r < 2; ++r) {
+          const int row = row0 + r, tz = row >> 3, ty = row & 7;
+          const int h = ((tz + kz) * HY + ty + ky) * HX + kx + a_vox;
+          uint32_t a[4];
+          ldsm_x4(s_a + swz(h, kc * 2 + a_chk), a[0], a[1], a[2], a[3]);
+#pragma unroll
+          for (int nt = 0; nt < 4; ++nt) mma_bf16(acc[r][nt], a, b[nt][0], b[nt][1]);
+        }
+      }
+    }
+
+#pragma unroll
+    for (int r = 0; r < 2; ++r) {
+      const int row = row0 + r;
+      const int z = z0 + (row >> 3), y = y0 + (row & 7);
+#pragma unroll
+      for (int hf = 0; hf < 2; ++hf) {
+        const int x = x0 + g + hf * 8;
+        if (!inside(d, z, y, x)) continue;
+        const size_t base = vox(d, z, y, x) * C;
+#pragma unroll
+        for (int nt = 0; nt < 4; ++nt) {
+          const int n = nt * 8 + tq * 2;
+          float v0 = acc[r][nt][hf * 2], v1 = acc[r][nt][hf * 2 + 1];
+          if (EPI == EPI_MASK) {
+            if (mask) {
+              const float2 m = __bfloat1622float2(*reinterpret_cast<const bf162*>(mask + base + n));
+              if (!(m.x > 0.f)) v0 = 0.f;
+              if (!(m.y > 0.f)) v1 = 0.f;
+            }
+          } else {
+            v0 += bn[nt][0];
+            v1 += bn[nt][1];
+            if (EPI == EPI_RELU) {
+              v0 = fmaxf(v0, 0.f);
+              v1 = fmaxf(v1, 0.f);
+            }
+          }
+          *reinterpret_cast<bf162*>(out + base + n) = __floats2bfloat162_rn(v0, v1);
+        }
+      }
+    }
+  }
+}
+
+// Weight (and bias) gradient of a 32 -> 32 layer: part[b][tap][co][ci] =
+// sum over the voxels of block b's tiles of dz[p][co] a[p + d(tap)][ci].  Grid
+// (P, 3): blockIdx.y is the tap's channel offset, warp w (9 per block) its row
+// and column offsets.  Block (b, 1) warp 0 also sums dz[p][co] into bpart[b][co].
+__global__ void __launch_bounds__(288)
+k_wgrad_tc(const bf16* __restrict__ a, const bf16* __restrict__ dz, float* __restrict__ part,
+           float* __restrict__ bpart, Dims d) {
+  __shared__ __align__(128) unsigned char s_d[TV * ROWB];
+  __shared__ __align__(128) unsigned char s_a[TZ * HY * HX * ROWB];
+  const int kz = blockIdx.y, warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int ky = warp / 3, kx = warp % 3;
+  const int g = lane >> 2, tq = lane & 3;
+  const uint32_t sd = smem_u32(s_d), sa = smem_u32(s_a);
+  const int a_vox = (lane & 7) + ((lane >> 4) & 1) * 8;   // transposed A: rows are voxels
+  const int a_chk = (lane >> 3) & 1;
+  const int b_vox = (lane & 7) + ((lane >> 3) & 1) * 8;
+  const int b_chk = lane >> 4;
+  const bool do_bias = bpart != nullptr && kz == 1 && warp == 0;
+  float acc[2][4][4];
+#pragma unroll
+  for (int mt = 0; mt < 2; ++mt)
+#pragma unroll
+    for (int nt = 0; nt < 4; ++nt)
+#pragma unroll
+      for (int e = 0; e < 4; ++e) acc[mt][nt][e] = 0.f;
+  float bacc = 0.f;
+
+  for (int tile = blockIdx.x; tile < d.ntiles; tile += gridDim.x) {
+    int z0, y0, x0;
+    tile_origin(tile, d, z0, y0, x0);
+    __syncthreads();
+    load_map_tile(sd, dz, d, z0, y0, x0);
+    load_map_halo<TZ>(sa, a, d, z0 + kz - 1, y0, x0);
+    cp_async_wait_all();
+    __syncthreads();
+#pragma unroll 2
+    for (int row = 0; row < TZ * TY; ++row) {
+      const int tz = row >> 3, ty = row & 7;
+      uint32_t af[2][4], bfr[4][2];
+#pragma unroll
+      for (int mt = 0; mt < 2; ++mt)
+        ldsm_x4_t(sd + swz(row * TX + a_vox, mt * 2 + a_chk), af[mt][0], af[mt][1], af[mt][2], af[mt][3]);
+      const int hb = (tz * HY + ty + ky) * HX + kx;
+#pragma unroll
+      for (int p = 0; p < 2; ++p)
+        ldsm_x4_t(sa + swz(hb + b_vox, 2 * p + b_chk), bfr[2 * p][0], bfr[2 * p][1], bfr[2 * p + 1][0],
+                  bfr[2 * p + 1][1]);
+#pragma unroll
+      for (int mt = 0; mt < 2; ++mt)
+#pragma unroll
+        for (int nt = 0; nt < 4; ++nt) mma_bf16(acc[mt][nt], af[mt], bfr[nt][0], bfr[nt][1]);
+    }
+    if (do_bias) {
+      for (int v = 0; v < TV; ++v)
+        bacc += __bfloat162float(*reinterpret_cast<const bf16*>(s_d + swz(v, lane >> 3) + (lane & 7) * 2));
+    }
+  }
+  const int t = kz * 9 + warp;
+  float* pp = part + ((size_t)blockIdx.x * NTAP + t) * (C * C);
+#pragma unroll
+  for (int mt = 0; mt < 2; ++mt)
+#pragma unroll
+    for (int nt = 0; nt < 4; ++nt) {
+      const int co = mt * 16 + g, ci = nt * 8 + tq * 2;
+      *reinterpret_cast<float2*>(pp + co * C + ci) = make_float2(acc[mt][nt][0], acc[mt][nt][1]);
+      *reinterpret_cast<float2*>(pp + (co + 8) * C + ci) = make_float2(acc[mt][nt][2], acc[mt][nt][3]);
+    }
+  if (do_bias) bpart[(size_t)blockIdx.x * C + lane] = bacc;
+}
+
+// ------------------------------------------------------------------ first and last layers (CUDA cores)
+
+// Thread -> voxel (tz, ty, tx) of the tile.
+__device__ __forceinline__ void thread_voxel(int& tz, int& ty, int& tx) {
+  tx = threadIdx.x & 15;
+  ty = (threadIdx.x >> 4) & 7;
+  tz = threadIdx.x >> 7;
+}
+
+// a1[p][co] = relu(b[co] + sum_tap a0[p + d(tap)] w[tap][co]).
+__global__ void __launch_bounds__(256)
+k_first_fwd(const bf16* __restrict__ a0, const float* __restrict__ w, const float* __restrict__ b,
+            bf16* __restrict__ a1, Dims d) {
+  __shared__ __align__(16) float s_w[NTAP * C];
+  __shared__ float s_b[C];
+  __shared__ float s_h[HV];
+  for (int i = threadIdx.x; i < NTAP * C; i += blockDim.x) s_w[i] = w[i];
+  if (threadIdx.x < C) s_b[threadIdx.x] = b[threadIdx.x];
+  int tz, ty, tx;
+  thread_voxel(tz, ty, tx);
+  for (int tile = blockIdx.x; tile < d.ntiles; tile += gridDim.x) {
+    int z0, y0, x0;
+    tile_origin(tile, d, z0, y0, x0);
+    __syncthreads();
+    load_scalar_halo(s_h, a0, d, z0, y0, x0);
+    __syncthreads();
+    float acc[C];
+#pragma unroll
+    for (int c = 0; c < C; ++c) acc[c] = s_b[c];
+#pragma unroll 1
+    for (int t = 0; t < NTAP; ++t) {
+      const int kz = t / 9, ky = (t / 3) % 3, kx = t % 3;
+      const float av = s_h[((tz + kz) * HY + ty + ky) * HX + tx + kx];
+      const float4* wr = reinterpret_cast<const float4*>(s_w + t * C);
+#pragma unroll
+      for (int q = 0; q < C / 4; ++q) {
+        const float4 wv = wr[q];
+        acc[4 * q] = fmaf(av, wv.x, acc[4 * q]);
+        acc[4 * q + 1] = fmaf(av, wv.y, acc[4 * q + 1]);
+        acc[4 * q + 2] = fmaf(av, wv.z, acc[4 * q + 2]);
+        acc[4 * q + 3] = fmaf(av, wv.w, acc[4 * q + 3]);
+      }
+    }
+    const int z = z0 + tz, y = y0 + ty, x = x0 + tx;
+    if (inside(d, z, y, x)) {
+#pragma unroll
+      for (int c = 0; c < C; ++c) acc[c] = fmaxf(acc[c], 0.f);
+      uint4* o = reinterpret_cast<uint4*>(a1 + vox(d, z, y, x) * C);
+#pragma unroll
+      for (int q = 0; q < 4; ++q) o[q] = pack8(acc + 8 * q);
+    }
+  }
+}
+
+// z6[p] = b + sum_tap sum_ci a5[p + d(tap)][ci] w[tap][ci].
+// TRAIN = 0: out[p] = max(s z6, 0).  TRAIN = 1: r = z6 - target/s, out[p] =
+// 2 r / V (the loss gradient), lpart[block] = (sum r^2, sum r).
+template <int TRAIN>
+__global__ void __launch_bounds__(256)
+k_last_fwd(const bf16* __restrict__ a5, const float* __restrict__ w, const float* __restrict__ b,
+           const float* __restrict__ target, const float* __restrict__ s_ptr, float* __restrict__ out,
+           double* __restrict__ lpart, Dims d) {
+  extern __shared__ __align__(128) unsigned char smem[];
+  const uint32_t s_a = smem_u32(smem);
+  float* s_w = reinterpret_cast<float*>(smem + HV * ROWB);
+  __shared__ double s_red[32];
+  for (int i = threadIdx.x; i < NTAP * C; i += blockDim.x) s_w[i] = w[i];
+  const float bias = b[0];
+  const float s = *s_ptr;
+  const float inv_s = 1.0f / s;
+  const float gscale = (float)(2.0 / (double)d.nvox);
+  int tz, ty, tx;
+  thread_voxel(tz, ty, tx);
+  double l2 = 0.0, l1 = 0.0;
+  for (int tile = blockIdx.x; tile < d.ntiles; tile += gridDim.x) {
+    int z0, y0, x0;
+    tile_origin(tile, d, z0, y0, x0);
+    __syncthreads();
+    load_map_halo<HZ>(s_a, a5, d, z0 - 1, y0, x0);
+    cp_async_wait_all();
+    __syncthreads();
+    float acc = bias;
+#pragma unroll 1
+    for (int t = 0; t < NTAP; ++t) {
+      const int kz = t / 9, ky = (t / 3) % 3, kx = t % 3;
+      const int h = ((tz + kz) * HY + ty + ky) * HX + tx + kx;
+#pragma unroll
+      for (int c = 0; c < 4; ++c) {
+        uint4 q;
+        asm volatile("ld.shared.v4.u32 {%0,%1,%2,%3}, [%4];\n"
+                     : "=r"(q.x), "=r"(q.y), "=r"(q.z), "=r"(q.w) : "r"(s_a + swz(h, c)));
+        float f[8];
+        unpack8(q, f);
+#pragma unroll
+        for (int e = 0; e < 8; ++e) acc = fmaf(f[e], s_w[t * C + c * 8 + e], acc);
+      }
+    }
+    const int z = z0 + tz, y = y0 + ty, x = x0 + tx;
+    if (inside(d, z, y, x)) {
+      const size_t v = vox(d, z, y, x);
+      if (TRAIN) {
+        const float r = acc - target[v] * inv_s;
+        out[v] = gscale * r;
+        l2 += (double)r * r;
+        l1 += r;
+      } else {
+        out[v] = fmaxf(s * acc, 0.f);
+      }
+    }
+  }
+  if (TRAIN) {
+    const double t2 = muffin::block_sum(l2, s_red);
+    __syncthreads();
+    const double t1 = muffin::block_sum(l1, s_red);
+    if (threadIdx.x == 0) {
+      lpart[2 * blockIdx.x] = t2;
+      lpart[2 * blockIdx.x + 1] = t1;
+    }
+  }
+}
+
+// g5[p][ci] = (a5[p][ci] > 0) * sum_tap d6[p - d(tap)] w[tap][ci].
+__global__ void __launch_bounds__(256)
+k_last_bwd_data(const float* __restrict__ d6, const float* __restrict__ w, const bf16* __restrict__ a5,
+                bf16* __restrict__ g5, Dims d) {
+  __shared__ __align__(16) float s_w[NTAP * C];
+  __shared__ float s_h[HV];
+  for (int i = threadIdx.x; i < NTAP * C; i += blockDim.x) s_w[i] = w[i];
+  int tz, ty, tx;
+  thread_voxel(tz, ty, tx);
+  for (int tile = blockIdx.x; tile < d.ntiles; tile += gridDim.x) {
+    int z0, y0, x0;
+    tile_origin(tile, d, z0, y0, x0);
+    __syncthreads();
+    load_scalar_halo(s_h, d6, d, z0, y0, x0);
+    __syncthreads();
+    float acc[C];
+#pragma unroll
+    for (int c = 0; c < C; ++c) acc[c] = 0.f;
+#pragma unroll 1
+    for (int t = 0; t < NTAP; ++t) {
+      const int kz = t / 9, ky = (t / 3) % 3, kx = t % 3;
+      const float dv = s_h[((tz + 2 - kz) * HY + ty + 2 - ky) * HX + tx + 2 - kx];
+      const float4* wr = reinterpret_cast<const float4*>(s_w + t * C);
+#pragma unroll
+      for (int q = 0; q < C / 4; ++q) {
+        const float4 wv = wr[q];
+        acc[4 * q] = fmaf(dv, wv.x, acc[4 * q]);
+        acc[4 * q + 1] = fmaf(dv, wv.y, acc[4 * q + 1]);
+        acc[4 * q + 2] = fmaf(dv, wv.z, acc[4 * q + 2]);
+        acc[4 * q + 3] = fmaf(dv, wv.w, acc[4 * q + 3]);
+      }
+    }
+    const int z = z0 + tz, y = y0 + ty, x = x0 + tx;
+    if (inside(d, z, y, x)) {
+      const size_t v = vox(d, z, y, x);
+      const uint4* m = reinterpret_cast<const uint4*>(a5 + v * C);
+      uint4* o = reinterpret_cast<uint4*>(g5 + v * C);
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        float mf[8];
+        unpack8(m[q], mf);
+#pragma unroll
+        for (int e = 0; e < 8; ++e)
+          if (!(mf[e] > 0.f)) acc[8 * q + e] = 0.f;
+        o[q] = pack8(acc + 8 * q);
+      }
+    }
+  }
+}
+
+// part[b][tap][co] = sum_p g1[p][co] a0[p + d(tap)]; bpart[b][co] = sum_p g1[p][co].
+// 864 threads: thread (tap, co).
+__global__ void __launch_bounds__(864)
+k_wgrad_first(const bf16* __restrict__ a0, const bf16* __restrict__ g1, float* __restrict__ part,
+              float* __restrict__ bpart, Dims d) {
+  __shared__ float s_h[HV];
+  __shared__ __align__(16) float s_g[TV * C];
+  const int t = threadIdx.x >> 5, co = threadIdx.x & 31;
+  const int kz = t / 9, ky = (t / 3) % 3, kx = t % 3;
+  float acc = 0.f, bacc = 0.f;
+  for (int tile = blockIdx.x; tile < d.ntiles; tile += gridDim.x) {
+    int z0, y0, x0;
+    tile_origin(tile, d, z0, y0, x0);
+    __syncthreads();
+    load_scalar_halo(s_h, a0, d, z0, y0, x0);
+    for (int i = threadIdx.x; i < TV * 4; i += blockDim.x) {
+      const int c = i & 3, r = i >> 2;
+      const int gz = z0 + (r >> 7), gy = y0 + ((r >> 4) & 7), gx = x0 + (r & 15);
+      float f[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+      if (inside(d, gz, gy, gx)) unpack8(*reinterpret_cast<const uint4*>(g1 + vox(d, gz, gy, gx) * C + c * 8), f);
+      float4* dst = reinterpret_cast<float4*>(s_g + r * C + c * 8);
+      dst[0] = make_float4(f[0], f[1], f[2], f[3]);
+      dst[1] = make_float4(f[4], f[5], f[6], f[7]);
+    }
+    __syncthreads();
+#pragma unroll 4
+    for (int v = 0; v < TV; ++v) {
+      const int vtx = v & 15, vty = (v >> 4) & 7, vtz = v >> 7;
+      acc = fmaf(s_g[v * C + co], s_h[((vtz + kz) * HY + vty + ky) * HX + vtx + kx], acc);
+    }
+    if (t == 0)
+      for (int v = 0; v < TV; ++v) bacc += s_g[v * C + co];
+  }
+  part[(size_t)blockIdx.x * (NTAP * C) + t * C + co] = acc;
+  if (t == 0) bpart[(size_t)blockIdx.x * C + co] = bacc;
+}
+
+// part[b][tap][ci] = sum_p d6[p] a5[p + d(tap)][ci].  864 threads: thread (tap, ci).
+__global__ void __launch_bounds__(864)
+k_wgrad_last(const float* __restrict__ d6, const bf16* __restrict__ a5, float* __restrict__ part, Dims d) {
+  __shared__ __align__(128) unsigned char s_a[HV * ROWB];
+  __shared__ float s_d[TV];
+  const uint32_t sa = smem_u32(s_a);
+  const int t = threadIdx.x >> 5, ci = threadIdx.x & 31;
+  const int kz = t / 9, ky = (t / 3) % 3, kx = t % 3;
+  float acc = 0.f;
+  for (int tile = blockIdx.x; tile < d.ntiles; tile += gridDim.x) {
+    int z0, y0, x0;
+    tile_origin(tile, d, z0, y0, x0);
+    __syncthreads();
+    load_map_halo<HZ>(sa, a5, d, z0 - 1, y0, x0);
+    for (int r = threadIdx.x; r < TV; r += blockDim.x) {
+      const int gz = z0 + (r >> 7), gy = y0 + ((r >> 4) & 7), gx = x0 + (r & 15);
+      s_d[r] = inside(d, gz, gy, gx) ? d6[vox(d, gz, gy, gx)] : 0.f;
+    }
+    cp_async_wait_all();
+    __syncthreads();
+#pragma unroll 4
+    for (int v = 0; v < TV; ++v) {
+      const int vtx = v & 15, vty = (v >> 4) & 7, vtz = v >> 7;
+      const int h = ((vtz + kz) * HY + vty + ky) * HX + vtx + kx;
+      const float av = __bfloat162float(*reinterpret_cast<const bf16*>(s_a + swz(h, ci >> 3) + (ci & 7) * 2));
+      acc = fmaf(s_d[v], av, acc);
+    }
+  }
+  part[(size_t)blockIdx.x * (NTAP * C) + t * C + ci] = acc;
+}
+
+// ------------------------------------------------------------------ reductions, input, parameters
+
+enum { MAP_PLAIN = 0, MAP_MID = 1, MAP_FIRST = 2, MAP_LAST = 3 };
+
+// out[map(i)] = sum_b part[b*n + i] (fixed order, double accumulation).
+// MAP_MID: i = (tap*32 + co)*32 + ci -> (co*32 + ci)*27 + tap; MAP_FIRST:
+// i = tap*32 + co -> co*27 + tap; MAP_LAST: i = tap*32 + ci -> ci*27 + tap.
+__global__ void k_reduce_part(const float* __restrict__ part, int P, int n, float* __restrict__ out, int map) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  double s = 0.0;
+  for (int b = 0; b < P; ++b) s += part[(size_t)b * n + i];
+  int j = i;
+  if (map == MAP_MID) {
+    const int t = i >> 10, co = (i >> 5) & 31, ci = i & 31;
+    j = (co * C + ci) * NTAP + t;
+  } else if (map == MAP_FIRST || map == MAP_LAST) {
+    const int t = i >> 5, c = i & 31;
+    j = c * NTAP + t;
+  }
+  out[j] = (float)s;
+}
+
+// loss = sum r^2 / V; gradient of the last bias = 2 sum r / V.
+__global__ void k_loss_final(const double* __restrict__ lpart, int P, long long nvox, double* __restrict__ loss,
+                             float* __restrict__ grad_b6) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  double l2 = 0.0, l1 = 0.0;
+  for (int b = 0; b < P; ++b) {
+    l2 += lpart[2 * b];
+    l1 += lpart[2 * b + 1];
+  }
+  if (loss) *loss = l2 / (double)nvox;
+  if (grad_b6) *grad_b6 = (float)(2.0 * l1 / (double)nvox);
+}
+
+__global__ void k_maxabs_part(const float* __restrict__ y, long long n, float* __restrict__ part) {
+  float m = 0.f;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+    m = fmaxf(m, fabsf(y[i]));
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_down_sync(0xffffffffu, m, o));
+  __shared__ float s[32];
+  if ((threadIdx.x & 31) == 0) s[threadIdx.x >> 5] = m;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    float r = 0.f;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) r = fmaxf(r, s[w]);
+    part[blockIdx.x] = r;
+  }
+}
+
+// s = max |y| (1 if the cube is zero); a0 = bf16(y / s).
+__global__ void k_scale_final(const float* __restrict__ part, int P, float* __restrict__ s) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  float m = 0.f;
+  for (int b = 0; b < P; ++b) m = fmaxf(m, part[b]);
+  *s = m > 0.f ? m : 1.f;
+}
+
+__global__ void k_prep_input(const float* __restrict__ y, const float* __restrict__ s, bf16* __restrict__ a0,
+                             long long n) {
+  const float inv = 1.0f / *s;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+    a0[i] = __float2bfloat16_rn(y[i] * inv);
+}
+
+struct KernelWeights {
+  float* w1;    // [27][32] (tap, co), bfloat16 values
+  float* b1;    // [32]
+  bf16* wf;     // [4][27][32 co][32 ci]   forward operands of layers 2..5
+  bf16* wb;     // [4][27][32 ci][32 co]   flipped, transposed: input gradients
+  float* bm;    // [4][32]
+  float* w6;    // [27][32] (tap, ci), bfloat16 values
+  float* b6;    // [1]
+};
+
+__device__ __forceinline__ float round_bf16(float v) { return __bfloat162float(__float2bfloat16_rn(v)); }
+
+// Packed float32 parameters -> the layouts the kernels read.
+__global__ void k_unpack_params(const float* __restrict__ theta, KernelWeights kw) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  constexpr int L1 = NTAP * C + C;           // 896
+  constexpr int LM = WMID + C;               // 27680
+  constexpr int N = L1 + 4 * LM + NTAP * C + 1;
+  if (i >= N) return;
+  const float v = theta[i];
+  if (i < L1) {
+    if (i < NTAP * C) kw.w1[(i % NTAP) * C + i / NTAP] = round_bf16(v);
+    else kw.b1[i - NTAP * C] = v;
+    return;
+  }
+  int j = i - L1;
+  if (j < 4 * LM) {
+    const int l = j / LM, li = j % LM;
+    if (li < WMID) {
+      const int co = li / (C * NTAP), rem = li % (C * NTAP), ci = rem / NTAP, t = rem % NTAP;
+      const bf16 q = __float2bfloat16_rn(v);
+      kw.wf[(size_t)l * WMID + (t * C + co) * C + ci] = q;
+      kw.wb[(size_t)l * WMID + ((NTAP - 1 - t) * C + ci) * C + co] = q;
+    } else {
+      kw.bm[l * C + li - WMID] = v;
+    }
+    return;
+  }
+  j -= 4 * LM;
+  if (j < NTAP * C) kw.w6[(j % NTAP) * C + j / NTAP] = round_bf16(v);
+  else kw.b6[0] = v;
+}
+
+// One 32 -> 32 layer's weights [co][ci][27] float32 -> forward ([27][co][ci])
+// or input-gradient ([27 flipped][ci][co]) bfloat16 operands.
+__global__ void k_pack_layer(const float* __restrict__ w, bf16* __restrict__ out, int backward) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= WMID) return;
+  const int co = i / (C * NTAP), rem = i % (C * NTAP), ci = rem / NTAP, t = rem % NTAP;
+  const bf16 q = __float2bfloat16_rn(w[i]);
+  if (backward) out[((NTAP - 1 - t) * C + ci) * C + co] = q;
+  else out[(t * C + co) * C + ci] = q;
+}
+
+// Adam (Kingma and Ba 2015, Algorithm 1); c1 = 1/(1 - beta1^t), c2 = 1/(1 - beta2^t).
+__global__ void k_adam(float* __restrict__ theta, const float* __restrict__ g, float* __restrict__ m,
+                       float* __restrict__ v, int n, float lr, float c1, float c2) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const float gi = g[i];
+  const float mi = 0.9f * m[i] + 0.1f * gi;
+  const float vi = 0.999f * v[i] + 0.001f * gi * gi;
+  m[i] = mi;
+  v[i] = vi;
+  theta[i] -= lr * (mi * c1) / (sqrtf(vi * c2) + 1e-8f);
+}
+
+// ------------------------------------------------------------------ host side
+
+int param_count() {
+  int n = 0;
+  for (int k = 0; k < NLAYER; ++k) n += kCo[k] * kCi[k] * NTAP + kCo[k];
+  return n;
+}
+
+int w_offset(int k) {  // packed offset of layer k's weights
+  int n = 0;
+  for (int j = 0; j < k; ++j) n += kCo[j] * kCi[j] * NTAP + kCo[j];
+  return n;
+}
+int b_offset(int k) { return w_offset(k) + kCo[k] * kCi[k] * NTAP; }
+
+inline size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+bool dims_ok(int nz, int ny, int nx) {
+  if (nz < 1 || ny < 1 || nx < 1) return false;
+  const long long v = (long long)nz * ny * nx;
+  return v < (1LL << 31) / C;
+}
+
+int part_slots(const Dims& d) { return d.ntiles < kMaxPart ? d.ntiles : kMaxPart; }
+int loss_slots(const Dims& d) { return d.ntiles < kMaxLossPart ? d.ntiles : kMaxLossPart; }
+
+int sm_count() {
+  int dev = 0, n = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return 148;
+  if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n <= 0) return 148;
+  return n;
+}
+
+cudaError_t configure_once() {
+  static bool done = false;
+  static cudaError_t err = cudaSuccess;
+  if (done) return err;
+  done = true;
+  if ((err = muffin::allow_max_dyn_smem(k_conv_tc<EPI_RELU>)) != cudaSuccess) return err;
+  if ((err = muffin::allow_max_dyn_smem(k_conv_tc<EPI_BIAS>)) != cudaSuccess) return err;
+  if ((err = muffin::allow_max_dyn_smem(k_conv_tc<EPI_MASK>)) != cudaSuccess) return err;
+  if ((err = muffin::allow_max_dyn_smem(k_last_fwd<0>)) != cudaSuccess) return err;
+  err = muffin::allow_max_dyn_smem(k_last_fwd<1>);
+  return err;
+}
+
+// Launch helpers (all persistent: grids bounded by the tile count).
+void launch_conv(int epi, const bf16* in, const bf16* wk, const float* bias, const bf16* mask, bf16* out,
+                 const Dims& d, int sms, cudaStream_t st) {
+  const int grid = d.ntiles < 2 * sms ? d.ntiles : 2 * sms;
+  if (epi == EPI_RELU) k_conv_tc<EPI_RELU><<<grid, 256, conv_smem, st>>>(in, wk, bias, mask, out, d);
+  else if (epi == EPI_BIAS) k_conv_tc<EPI_BIAS><<<grid, 256, conv_smem, st>>>(in, wk, bias, mask, out, d);
+  else k_conv_tc<EPI_MASK><<<grid, 256, conv_smem, st>>>(in, wk, bias, mask, out, d);
+}
+
+void launch_wgrad_mid(const bf16* a, const bf16* dz, float* part, float* bpart, float* dw, float* db, const Dims& d,
+                      int sms, cudaStream_t st) {
+  int P = part_slots(d);
+  if (P > sms) P = sms;
+  k_wgrad_tc<<<dim3(P, 3), 288, 0, st>>>(a, dz, part, bpart, d);
+  k_reduce_part<<<(WMID + 255) / 256, 256, 0, st>>>(part, P, WMID, dw, MAP_MID);
+  if (db) k_reduce_part<<<1, 32, 0, st>>>(bpart, P, C, db, MAP_PLAIN);
+}
+
+}  // namespace mnet
+
+using namespace mnet;
+
+// ====================================================================== network context
+
+struct muffin_net {
+  int training = 0;
+  Dims d{};
+  cudaStream_t st = nullptr;
+  int sms = 148;
+  long long step = 0;
+  std::string err;
+  // parameters and optimiser
+  float *theta = nullptr, *mom1 = nullptr, *mom2 = nullptr, *grad = nullptr;
+  KernelWeights kw{};
+  // scalars and partials
+  float* s = nullptr;
+  float* mpart = nullptr;
+  double* lpart = nullptr;
+  double* loss = nullptr;
+  float* part = nullptr;
+  float* bpart = nullptr;
+  // maps
+  bf16* a0 = nullptr;
+  bf16* act = nullptr;   // training: a1..a5; inference: two ping-pong maps
+  bf16* gA = nullptr;
+  bf16* gB = nullptr;
+  float* d6 = nullptr;
+
+  bf16* map(int i) const { return act + (size_t)i * d.nvox * C; }
+};
+
+namespace {
+
+// Workspace carve-up; with base == nullptr only the size is computed.
+size_t net_layout(muffin_net* n, const Dims& d, int training, char* base) {
+  size_t off = 0;
+  auto take = [&](size_t bytes) -> char* {
+    char* p = base ? base + off : nullptr;
+    off = align256(off + bytes);
+    return p;
+  };
+  const int np = param_count();
+  const size_t V = (size_t)d.nvox;
+  float* theta = (float*)take(np * 4);
+  float* m1 = (float*)take(training ? np * 4 : 0);
+  float* m2 = (float*)take(training ? np * 4 : 0);
+  float* grad = (float*)take(training ? np * 4 : 0);
+  KernelWeights kw;
+  kw.w1 = (float*)take(NTAP * C * 4);
+  kw.b1 = (float*)take(C * 4);
+  kw.wf = (bf16*)take(4 * WMID * 2);
+  kw.wb = (bf16*)take(4 * WMID * 2);
+  kw.bm = (float*)take(4 * C * 4);
+  kw.w6 = (float*)take(NTAP * C * 4);
+  kw.b6 = (float*)take(4);
+  float* s = (float*)take(4);
+  float* mpart = (float*)take(kMaxLossPart * 4);
+  double* lpart = (double*)take(2 * kMaxLossPart * 8);
+  double* loss = (double*)take(8);
+  const int P = part_slots(d);
+  float* part = (float*)take(training ? (size_t)P * WMID * 4 : 0);
+  float* bpart = (float*)take(training ? (size_t)P * C * 4 : 0);
+  bf16* a0 = (bf16*)take(V * 2);
+  bf16* act = (bf16*)take((training ? 5 : 2) * V * C * 2);
+  bf16* gA = (bf16*)take(training ? V * C * 2 : 0);
+  bf16* gB = (bf16*)take(training ? V * C * 2 : 0);
+  float* d6 = (float*)take(training ? V * 4 : 0);
+  if (n) {
+    n->theta = theta; n->mom1 = m1; n->mom2 = m2; n->grad = grad; n->kw = kw;
+    n->s = s; n->mpart = mpart; n->lpart = lpart; n->loss = loss; n->part = part; n->bpart = bpart;
+    n->a0 = a0; n->act = act; n->gA = gA; n->gB = gB; n->d6 = d6;
+  }
+  return off;
+}
+
+int fail(muffin_net* n, int code, const std::string& msg) {
+  if (n) n->err = msg;
+  return code;
+}
+
+int cuda_check(muffin_net* n, const char* what) {
+  const cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return fail(n, MUFFIN_ERR_CUDA, std::string(what) + ": " + cudaGetErrorString(e));
+  return MUFFIN_OK;
+}
+
+// s, a0 and the forward pass through layer 5 (training keeps every map).
+void forward_to_a5(muffin_net* n, const float* y) {
+  const Dims& d = n->d;
+  const int PL = loss_slots(d);
+  const int grid_s = (int)((d.nvox + 255) / 256 < PL ? (d.nvox + 255) / 256 : PL);
+  k_maxabs_part<<<grid_s, 256, 0, n->st>>>(y, d.nvox, n->mpart);
+  k_scale_final<<<1, 32, 0, n->st>>>(n->mpart, grid_s, n->s);
+  const int grid_p = (int)((d.nvox + 255) / 256 < 4 * n->sms ? (d.nvox + 255) / 256 : 4 * n->sms);
+  k_prep_input<<<grid_p, 256, 0, n->st>>>(y, n->s, n->a0, d.nvox);
+  const int gsimt = d.ntiles < 4 * n->sms ? d.ntiles : 4 * n->sms;
+  bf16* out = n->map(0);
+  k_first_fwd<<<gsimt, 256, 0, n->st>>>(n->a0, n->kw.w1, n->kw.b1, out, d);
+  for (int l = 0; l < 4; ++l) {
+    bf16* in = out;
+    out = n->training ? n->map(l + 1) : n->map((l + 1) & 1);
+    launch_conv(EPI_RELU, in, n->kw.wf + (size_t)l * WMID, n->kw.bm + l * C, nullptr, out, d, n->sms, n->st);
+  }
+}
+
+bf16* a5_of(muffin_net* n) { return n->training ? n->map(4) : n->map(0); }
+
+// Loss and gradient into n->grad (training contexts).
+void loss_and_grad(muffin_net* n, const float* y, const float* t) {
+  const Dims& d = n->d;
+  forward_to_a5(n, y);
+  bf16* a5 = a5_of(n);
+  const int PL = loss_slots(d);
+  k_last_fwd<1><<<PL, 256, last_smem, n->st>>>(a5, n->kw.w6, n->kw.b6, t, n->s, n->d6, n->lpart, d);
+  k_loss_final<<<1, 32, 0, n->st>>>(n->lpart, PL, d.nvox, n->loss, n->grad + b_offset(5));
+  int P = part_slots(d);
+  if (P > 2 * n->sms) P = 2 * n->sms;
+  k_wgrad_last<<<P, 864, 0, n->st>>>(n->d6, a5, n->part, d);
+  k_reduce_part<<<(NTAP * C + 255) / 256, 256, 0, n->st>>>(n->part, P, NTAP * C, n->grad + w_offset(5), MAP_LAST);
+  const int gsimt = d.ntiles < 4 * n->sms ? d.ntiles : 4 * n->sms;
+  bf16* g = n->gA;
+  bf16* other = n->gB;
+  k_last_bwd_data<<<gsimt, 256, 0, n->st>>>(n->d6, n->kw.w6, a5, g, d);
+  for (int k = 4; k >= 1; --k) {          // layers 5..2 (index k), input map a_k = map(k - 1)
+    const bf16* a_in = n->map(k - 1);
+    launch_wgrad_mid(a_in, g, n->part, n->bpart, n->grad + w_offset(k), n->grad + b_offset(k), d, n->sms, n->st);
+    launch_conv(EPI_MASK, g, n->kw.wb + (size_t)(k - 1) * WMID, nullptr, a_in, other, d, n->sms, n->st);
+    bf16* tmp = g; g = other; other = tmp;
+  }
+  P = part_slots(d);
+  if (P > 2 * n->sms) P = 2 * n->sms;
+  k_wgrad_first<<<P, 864, 0, n->st>>>(n->a0, g, n->part, n->bpart, d);
+  k_reduce_part<<<(NTAP * C + 255) / 256, 256, 0, n->st>>>(n->part, P, NTAP * C, n->grad + w_offset(0), MAP_FIRST);
+  k_reduce_part<<<1, 32, 0, n->st>>>(n->bpart, P, C, n->grad + b_offset(0), MAP_PLAIN);
+}
+
+void unpack_params(muffin_net* n) {
+  const int np = param_count();
+  k_unpack_params<<<(np + 255) / 256, 256, 0, n->st>>>(n->theta, n->kw);
+}
+
+}  // namespace
+
+extern "C" {
+
+int muffin_net_num_params(void) { return param_count(); }
+
+size_t muffin_net_workspace_bytes(int nz, int ny, int nx, int training) {
+  if (!dims_ok(nz, ny, nx)) return 0;
+  return net_layout(nullptr, make_dims(nz, ny, nx), training != 0, nullptr);
+}
+
+int muffin_net_create(muffin_net** out, int nz, int ny, int nx, int training, void* d_ws, size_t ws_bytes,
+                      cudaStream_t stream) {
+  if (!out) return MUFFIN_ERR_ARG;
+  *out = nullptr;
+  if (!dims_ok(nz, ny, nx)) return MUFFIN_ERR_ARG;
+  if (!d_ws || ((uintptr_t)d_ws & 255)) return MUFFIN_ERR_ARG;
+  const Dims d = make_dims(nz, ny, nx);
+  const size_t need = net_layout(nullptr, d, training != 0, nullptr);
+  if (ws_bytes < need) return MUFFIN_ERR_NOMEM;
+  if (configure_once() != cudaSuccess) return MUFFIN_ERR_CUDA;
+  muffin_net* n = new muffin_net();
+  n->training = training != 0;
+  n->d = d;
+  n->st = stream;
+  n->sms = sm_count();
+  net_layout(n, d, n->training, (char*)d_ws);
+  const int np = param_count();
+  cudaMemsetAsync(n->theta, 0, np * 4, stream);
+  if (n->training) {
+    cudaMemsetAsync(n->mom1, 0, np * 4, stream);
+    cudaMemsetAsync(n->mom2, 0, np * 4, stream);
+  }
+  unpack_params(n);
+  if (cudaGetLastError() != cudaSuccess) {
+    delete n;
+    return MUFFIN_ERR_CUDA;
+  }
+  *out = n;
+  return MUFFIN_OK;
+}
+
+int muffin_net_set_params(muffin_net* n, const float* d_theta) {
+  if (!n) return MUFFIN_ERR_ARG;
+  if (!d_theta) return fail(n, MUFFIN_ERR_ARG, "d_theta is NULL");
+  const int np = param_count();
+  cudaMemcpyAsync(n->theta, d_theta, np * 4, cudaMemcpyDeviceToDevice, n->st);
+  if (n->training) {
+    cudaMemsetAsync(n->mom1, 0, np * 4, n->st);
+    cudaMemsetAsync(n->mom2, 0, np * 4, n->st);
+  }
+  n->step = 0;
+  unpack_params(n);
+  return cuda_check(n, "muffin_net_set_params");
+}
+
+int muffin_net_get_params(const muffin_net* n, float* d_theta) {
+  if (!n || !d_theta) return MUFFIN_ERR_ARG;
+  cudaMemcpyAsync(d_theta, n->theta, param_count() * 4, cudaMemcpyDeviceToDevice, n->st);
+  return cuda_check(const_cast<muffin_net*>(n), "muffin_net_get_params");
+}
+
+int muffin_net_predict(muffin_net* n, const float* d_dirty, float* d_x) {
+  if (!n) return MUFFIN_ERR_ARG;
+  if (!d_dirty || !d_x) return fail(n, MUFFIN_ERR_ARG, "NULL cube pointer");
+  forward_to_a5(n, d_dirty);
+  const int PL = loss_slots(n->d);
+  k_last_fwd<0><<<PL, 256, last_smem, n->st>>>(a5_of(n), n->kw.w6, n->kw.b6, nullptr, n->s, d_x, nullptr, n->d);
+  return cuda_check(n, "muffin_net_predict");
+}
+
+int muffin_net_loss_grad(muffin_net* n, const float* d_dirty, const float* d_target, float* d_grad, double* h_loss) {
+  if (!n) return MUFFIN_ERR_ARG;
+  if (!n->training) return fail(n, MUFFIN_ERR_STATE, "not a training context");
+  if (!d_dirty || !d_target || !d_grad) return fail(n, MUFFIN_ERR_ARG, "NULL pointer");
+  loss_and_grad(n, d_dirty, d_target);
+  cudaMemcpyAsync(d_grad, n->grad, param_count() * 4, cudaMemcpyDeviceToDevice, n->st);
+  int r = cuda_check(n, "muffin_net_loss_grad");
+  if (r != MUFFIN_OK) return r;
+  if (h_loss) {
+    cudaMemcpyAsync(h_loss, n->loss, 8, cudaMemcpyDeviceToHost, n->st);
+    const cudaError_t e = cudaStreamSynchronize(n->st);
+    if (e != cudaSuccess) return fail(n, MUFFIN_ERR_CUDA, std::string("muffin_net_loss_grad: ") + cudaGetErrorString(e));
+  }
+  return MUFFIN_OK;
+}
+
+int muffin_net_train_step(muffin_net* n, const float* d_dirty, const float* d_target, float lr, double* d_loss) {
+  if (!n) return MUFFIN_ERR_ARG;
+  if (!n->training) return fail(n, MUFFIN_ERR_STATE, "not a training context");
+  if (!d_dirty || !d_target) return fail(n, MUFFIN_ERR_ARG, "NULL pointer");
+  if (!(lr >= 0.f) || !std::isfinite(lr)) return fail(n, MUFFIN_ERR_ARG, "learning rate must be finite and >= 0");
+  loss_and_grad(n, d_dirty, d_target);
+  if (d_loss) cudaMemcpyAsync(d_loss, n->loss, 8, cudaMemcpyDeviceToDevice, n->st);
+  n->step += 1;
+  const double c1 = 1.0 / (1.0 - std::pow(0.9, (double)n->step));
+  const double c2 = 1.0 / (1.0 - std::pow(0.999, (double)n->step));
+  const int np = param_count();
+  k_adam<<<(np + 255) / 256, 256, 0, n->st>>>(n->theta, n->grad, n->mom1, n->mom2, np, lr, (float)c1, (float)c2);
+  unpack_params(n);
+  return cuda_check(n, "muffin_net_train_step");
+}
+
+const char* muffin_net_last_error(const muffin_net* n) {
+  if (!n) return "invalid arguments to muffin_net_create (sizes, workspace alignment or size) or CUDA set-up failed";
+  return n->err.c_str();
+}
+
+void muffin_net_destroy(muffin_net* n) { delete n; }
+
+// ---------------------------------------------------------------------- single layers
+
+static thread_local std::string g_conv_err;
+
+static int conv_fail(int code, const std::string& msg) {
+  g_conv_err = msg;
+  return code;
+}
+
+static int conv_cuda(const char* what) {
+  const cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return conv_fail(MUFFIN_ERR_CUDA, std::string(what) + ": " + cudaGetErrorString(e));
+  return MUFFIN_OK;
+}
+
+static bool aligned16(const void* p) { return ((uintptr_t)p & 15) == 0; }
+
+size_t muffin_conv3d_scratch_bytes(int nz, int ny, int nx) {
+  if (!dims_ok(nz, ny, nx)) return 0;
+  const Dims d = make_dims(nz, ny, nx);
+  const int P = part_slots(d);
+  return align256(WMID * 2) + align256((size_t)P * WMID * 4) + align256((size_t)P * C * 4);
+}
+
+static int layer_args(const void* a, const void* b, int nz, int ny, int nx, void* scratch, size_t bytes) {
+  if (!dims_ok(nz, ny, nx)) return conv_fail(MUFFIN_ERR_ARG, "sizes must be >= 1 with nz*ny*nx*32 < 2^31");
+  if (!a || !b || !scratch) return conv_fail(MUFFIN_ERR_ARG, "NULL pointer");
+  if (!aligned16(a) || !aligned16(b) || ((uintptr_t)scratch & 255))
+    return conv_fail(MUFFIN_ERR_ARG, "maps must be 16-byte aligned, scratch 256-byte aligned");
+  if (bytes < muffin_conv3d_scratch_bytes(nz, ny, nx)) return conv_fail(MUFFIN_ERR_NOMEM, "scratch too small");
+  if (configure_once() != cudaSuccess) return conv_fail(MUFFIN_ERR_CUDA, "kernel attributes could not be set");
+  return MUFFIN_OK;
+}
+
+int muffin_conv3d_forward(const void* d_a, const float* d_w, const float* d_b, int relu, void* d_z, int nz, int ny,
+                          int nx, void* d_scratch, size_t scratch_bytes, cudaStream_t stream) {
+  int r = layer_args(d_a, d_z, nz, ny, nx, d_scratch, scratch_bytes);
+  if (r != MUFFIN_OK) return r;
+  if (!d_w) return conv_fail(MUFFIN_ERR_ARG, "NULL weights");
+  const Dims d = make_dims(nz, ny, nx);
+  bf16* wk = (bf16*)d_scratch;
+  k_pack_layer<<<(WMID + 255) / 256, 256, 0, stream>>>(d_w, wk, 0);
+  launch_conv(relu ? EPI_RELU : EPI_BIAS, (const bf16*)d_a, wk, d_b, nullptr, (bf16*)d_z, d, sm_count(), stream);
+  return conv_cuda("muffin_conv3d_forward");
+}
+
+int muffin_conv3d_backward_data(const void* d_dz, const float* d_w, const void* d_mask, void* d_da, int nz, int ny,
+                                int nx, void* d_scratch, size_t scratch_bytes, cudaStream_t stream) {
+  int r = layer_args(d_dz, d_da, nz, ny, nx, d_scratch, scratch_bytes);
+  if (r != MUFFIN_OK) return r;
+  if (!d_w) return conv_fail(MUFFIN_ERR_ARG, "NULL weights");
+  if (d_mask && !aligned16(d_mask)) return conv_fail(MUFFIN_ERR_ARG, "mask must be 16-byte aligned");
+  const Dims d = make_dims(nz, ny, nx);
+  bf16* wk = (bf16*)d_scratch;
+  k_pack_layer<<<(WMID + 255) / 256, 256, 0, stream>>>(d_w, wk, 1);
+  launch_conv(EPI_MASK, (const bf16*)d_dz, wk, nullptr, (const bf16*)d_mask, (bf16*)d_da, d, sm_count(), stream);
+  return conv_cuda("muffin_conv3d_backward_data");
+}
+
+int muffin_conv3d_backward_weights(const void* d_a, const void* d_dz, float* d_dw, float* d_db, int nz, int ny,
+                                   int nx, void* d_scratch, size_t scratch_bytes, cudaStream_t stream) {
+  int r = layer_args(d_a, d_dz, nz, ny, nx, d_scratch, scratch_bytes);
+  if (r != MUFFIN_OK) return r;
+  if (!d_dw) return conv_fail(MUFFIN_ERR_ARG, "NULL weight gradient");
+  const Dims d = make_dims(nz, ny, nx);
+  char* base = (char*)d_scratch + align256(WMID * 2);
+  const int P = part_slots(d);
+  float* part = (float*)base;
+  float* bpart = (float*)(base + align256((size_t)P * WMID * 4));
+  launch_wgrad_mid((const bf16*)d_a, (const bf16*)d_dz, part, bpart, d_dw, d_db, d, sm_count(), stream);
+  return conv_cuda("muffin_conv3d_backward_weights");
+}
+
+const char* muffin_conv3d_last_error(void) { return g_conv_err.c_str(); }
+
+}  // extern "C"

@@ -1,0 +1,209 @@
+"""Python binding of the warm-start network (include/muffin_net.h).
+
+Argument marshalling only: the forward pass, the loss, the gradients and Adam
+all run in libmuffin's CUDA kernels.  PyTorch provides the device memory
+(workspaces, cubes, parameter vectors) and the stream.  Like the rest of the
+package there is no CPU fallback: this module raises at import when the
+library is missing.
+"""
+from __future__ import annotations
+
+import ctypes
+
+import torch
+
+from . import muffin as _m
+
+_lib = _m.lib
+_P, _I, _S, _F = ctypes.c_void_p, ctypes.c_int, ctypes.c_size_t, ctypes.c_float
+_SIG = {
+    "muffin_net_num_params": (_I, []),
+    "muffin_net_workspace_bytes": (_S, [_I, _I, _I, _I]),
+    "muffin_net_create": (_I, [ctypes.POINTER(_P), _I, _I, _I, _I, _P, _S, _P]),
+    "muffin_net_set_params": (_I, [_P, _P]),
+    "muffin_net_get_params": (_I, [_P, _P]),
+    "muffin_net_predict": (_I, [_P, _P, _P]),
+    "muffin_net_loss_grad": (_I, [_P, _P, _P, _P, ctypes.POINTER(ctypes.c_double)]),
+    "muffin_net_train_step": (_I, [_P, _P, _P, _F, _P]),
+    "muffin_net_last_error": (ctypes.c_char_p, [_P]),
+    "muffin_net_destroy": (None, [_P]),
+    "muffin_conv3d_scratch_bytes": (_S, [_I, _I, _I]),
+    "muffin_conv3d_forward": (_I, [_P, _P, _P, _I, _P, _I, _I, _I, _P, _S, _P]),
+    "muffin_conv3d_backward_data": (_I, [_P, _P, _P, _P, _I, _I, _I, _P, _S, _P]),
+    "muffin_conv3d_backward_weights": (_I, [_P, _P, _P, _P, _I, _I, _I, _P, _S, _P]),
+    "muffin_conv3d_last_error": (ctypes.c_char_p, []),
+}
+for _name, (_res, _args) in _SIG.items():
+    _fn = getattr(_lib, _name)
+    _fn.restype = _res
+    _fn.argtypes = _args
+
+N_PARAMS = int(_lib.muffin_net_num_params())
+FEATURES = 32
+
+
+def _ptr(t):
+    return None if t is None else t.data_ptr()
+
+
+def _dev_f32(t: torch.Tensor, name: str) -> torch.Tensor:
+    if not (t.is_cuda and t.dtype == torch.float32 and t.is_contiguous()):
+        raise ValueError(f"{name} must be a contiguous float32 CUDA tensor")
+    return t
+
+
+def _map(t: torch.Tensor, shape, name: str) -> torch.Tensor:
+    if not (t.is_cuda and t.dtype == torch.bfloat16 and t.is_contiguous()) or tuple(t.shape) != tuple(shape):
+        raise ValueError(f"{name} must be a contiguous bfloat16 CUDA tensor of shape {tuple(shape)}")
+    return t
+
+
+class WarmStartNet:
+    """The network on nz x ny x nx cubes (a libmuffin network context)."""
+
+    def __init__(self, shape, training: bool = False, theta: torch.Tensor | None = None):
+        self.shape = tuple(int(s) for s in shape)
+        nz, ny, nx = self.shape
+        self.training = bool(training)
+        nbytes = int(_lib.muffin_net_workspace_bytes(nz, ny, nx, int(self.training)))
+        if nbytes == 0:
+            raise ValueError(f"invalid cube shape {self.shape}")
+        self._ws = torch.empty(nbytes, dtype=torch.uint8, device="cuda")
+        self._net = _P()
+        r = _lib.muffin_net_create(ctypes.byref(self._net), nz, ny, nx, int(self.training), self._ws.data_ptr(),
+                                   nbytes, torch.cuda.current_stream().cuda_stream)
+        if r != 0:
+            raise _m.MuffinError(r, _lib.muffin_net_last_error(None).decode())
+        if theta is not None:
+            self.set_params(theta)
+
+    def _check(self, r: int):
+        if r != 0:
+            raise _m.MuffinError(r, _lib.muffin_net_last_error(self._net).decode())
+
+    def _cube(self, t: torch.Tensor, name: str) -> torch.Tensor:
+        _dev_f32(t, name)
+        if tuple(t.shape) != self.shape:
+            raise ValueError(f"{name} has shape {tuple(t.shape)}, expected {self.shape}")
+        return t
+
+    def set_params(self, theta: torch.Tensor):
+        theta = _dev_f32(theta.reshape(-1), "theta")
+        if theta.numel() != N_PARAMS:
+            raise ValueError(f"theta has {theta.numel()} values, expected {N_PARAMS}")
+        self._check(_lib.muffin_net_set_params(self._net, theta.data_ptr()))
+
+    def get_params(self) -> torch.Tensor:
+        out = torch.empty(N_PARAMS, dtype=torch.float32, device="cuda")
+        self._check(_lib.muffin_net_get_params(self._net, out.data_ptr()))
+        return out
+
+    def predict(self, dirty: torch.Tensor, out: torch.Tensor | None = None) -> torch.Tensor:
+        self._cube(dirty, "dirty")
+        if out is None:
+            out = torch.empty_like(dirty)
+        self._cube(out, "out")
+        self._check(_lib.muffin_net_predict(self._net, dirty.data_ptr(), out.data_ptr()))
+        return out
+
+    def loss_grad(self, dirty: torch.Tensor, target: torch.Tensor) -> tuple[float, torch.Tensor]:
+        self._cube(dirty, "dirty")
+        self._cube(target, "target")
+        g = torch.empty(N_PARAMS, dtype=torch.float32, device="cuda")
+        loss = ctypes.c_double()
+        self._check(_lib.muffin_net_loss_grad(self._net, dirty.data_ptr(), target.data_ptr(), g.data_ptr(),
+                                              ctypes.byref(loss)))
+        return loss.value, g
+
+    def train_step(self, dirty: torch.Tensor, target: torch.Tensor, lr: float,
+                   loss_out: torch.Tensor | None = None):
+        """One Adam step; loss_out (a float64 CUDA scalar) receives the loss."""
+        self._cube(dirty, "dirty")
+        self._cube(target, "target")
+        if loss_out is not None and not (loss_out.is_cuda and loss_out.dtype == torch.float64):
+            raise ValueError("loss_out must be a float64 CUDA tensor")
+        self._check(_lib.muffin_net_train_step(self._net, dirty.data_ptr(), target.data_ptr(), float(lr),
+                                               _ptr(loss_out)))
+
+    def close(self):
+        if getattr(self, "_net", None) is not None and self._net.value:
+            _lib.muffin_net_destroy(self._net)
+            self._net = _P()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:  # noqa: BLE001
+            pass
+
+
+# ---------------------------------------------------------------- single 32 -> 32 layers
+
+def _scratch(nz, ny, nx) -> torch.Tensor:
+    return torch.empty(int(_lib.muffin_conv3d_scratch_bytes(nz, ny, nx)), dtype=torch.uint8, device="cuda")
+
+
+def _layer_check(r: int):
+    if r != 0:
+        raise _m.MuffinError(r, _lib.muffin_conv3d_last_error().decode())
+
+
+def conv3d_forward(a: torch.Tensor, w: torch.Tensor, b: torch.Tensor | None, relu: bool) -> torch.Tensor:
+    """z = act(conv(a, w) + b); a bfloat16 [nz][ny][nx][32], w float32 [32][32][3][3][3]."""
+    nz, ny, nx = a.shape[:3]
+    _map(a, (nz, ny, nx, FEATURES), "a")
+    w = _dev_f32(w.contiguous(), "w")
+    if b is not None:
+        b = _dev_f32(b.contiguous(), "b")
+    z = torch.empty_like(a)
+    s = _scratch(nz, ny, nx)
+    _layer_check(_lib.muffin_conv3d_forward(a.data_ptr(), w.data_ptr(), _ptr(b), int(relu), z.data_ptr(), nz, ny,
+                                            nx, s.data_ptr(), s.numel(), torch.cuda.current_stream().cuda_stream))
+    return z
+
+
+def conv3d_backward_data(dz: torch.Tensor, w: torch.Tensor, mask: torch.Tensor | None) -> torch.Tensor:
+    """da = (mask > 0) * conv^T(dz, w)."""
+    nz, ny, nx = dz.shape[:3]
+    _map(dz, (nz, ny, nx, FEATURES), "dz")
+    if mask is not None:
+        _map(mask, (nz, ny, nx, FEATURES), "mask")
+    w = _dev_f32(w.contiguous(), "w")
+    da = torch.empty_like(dz)
+    s = _scratch(nz, ny, nx)
+    _layer_check(_lib.muffin_conv3d_backward_data(dz.data_ptr(), w.data_ptr(), _ptr(mask), da.data_ptr(), nz, ny,
+                                                  nx, s.data_ptr(), s.numel(),
+                                                  torch.cuda.current_stream().cuda_stream))
+    return da
+
+
+def conv3d_backward_weights(a: torch.Tensor, dz: torch.Tensor) -> tuple[torch.Tensor, torch.Tensor]:
+    """(dw float32 [32][32][3][3][3], db float32 [32])."""
+    nz, ny, nx = a.shape[:3]
+    _map(a, (nz, ny, nx, FEATURES), "a")
+    _map(dz, (nz, ny, nx, FEATURES), "dz")
+    dw = torch.empty((FEATURES, FEATURES, 3, 3, 3), dtype=torch.float32, device="cuda")
+    db = torch.empty(FEATURES, dtype=torch.float32, device="cuda")
+    s = _scratch(nz, ny, nx)
+    _layer_check(_lib.muffin_conv3d_backward_weights(a.data_ptr(), dz.data_ptr(), dw.data_ptr(), db.data_ptr(), nz,
+                                                     ny, nx, s.data_ptr(), s.numel(),
+                                                     torch.cuda.current_stream().cuda_stream))
+    return dw, db
+
+
+# ---------------------------------------------------------------- warm start of Algorithm 1
+
+def warm_start(problem, net: WarmStartNet, dirty: torch.Tensor) -> dict:
+    """Start ``problem`` (a muffin.Muffin at pass 0) from the network's cube.
+
+    The plain method's start X = 0 stays the fallback and the judge: the
+    prediction is kept only if the objective of Eqs. 5-6 is lower there than
+    at X = 0.  Returns what was decided and both objectives."""
+    f0, _ = problem.objective()
+    x = net.predict(dirty)
+    problem.set_cube(x)
+    f1, _ = problem.objective()
+    used = f1 < f0
+    if not used:
+        problem.set_cube(torch.zeros_like(x))
+    return {"used": bool(used), "f_zero": f0, "f_net": f1}

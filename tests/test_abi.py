@@ -1,19 +1,23 @@
 """The C ABI without a GPU: the library loads, exports every entry point that
-include/muffin.h declares, and its host-side checks behave (no compute calls)."""
+a header under include/ declares, and its host-side checks behave (no compute
+calls)."""
 import ctypes
+import glob
 import os
 import re
 
 import pytest
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
-HEADER = os.path.join(ROOT, "include", "muffin.h")
+HEADERS = sorted(glob.glob(os.path.join(ROOT, "include", "*.h")))
 
 
 def declared_functions():
-    text = open(HEADER).read()
-    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
-    return sorted(set(re.findall(r"\b(muffin_[a-z0-9_]+)\s*\(", text)))
+    names = set()
+    for h in HEADERS:
+        text = re.sub(r"/\*.*?\*/", "", open(h).read(), flags=re.S)
+        names |= set(re.findall(r"\b(muffin_[a-z0-9_]+)\s*\(", text))
+    return sorted(names)
 
 
 @pytest.fixture(scope="module")
@@ -26,7 +30,7 @@ def so():
 
 def test_every_declared_symbol_is_exported(so):
     names = declared_functions()
-    assert len(names) >= 19
+    assert len(HEADERS) >= 2 and len(names) >= 30
     missing = [n for n in names if not hasattr(so, n)]
     assert not missing, missing
 
@@ -67,3 +71,26 @@ def test_init_rejects_bad_arguments_before_any_cuda_call():
     r = lib.muffin_init(ctypes.byref(ctx), ctypes.byref(p), 256, 0x1000, 16, None)
     assert r == -3
     assert lib.muffin_iterate(None, 1) == -1
+
+
+def test_net_sizes_and_create_argument_checks(so):
+    so.muffin_net_workspace_bytes.restype = ctypes.c_size_t
+    so.muffin_net_workspace_bytes.argtypes = [ctypes.c_int] * 4
+    so.muffin_conv3d_scratch_bytes.restype = ctypes.c_size_t
+    so.muffin_conv3d_scratch_bytes.argtypes = [ctypes.c_int] * 3
+    so.muffin_net_create.argtypes = [ctypes.POINTER(ctypes.c_void_p), ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                     ctypes.c_int, ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p]
+    assert so.muffin_net_num_params() == 112481
+    infer = so.muffin_net_workspace_bytes(64, 256, 256, 0)
+    train = so.muffin_net_workspace_bytes(64, 256, 256, 1)
+    V = 64 * 256 * 256
+    assert infer >= V * 2 + 2 * V * 64          # input map + two feature maps
+    assert train >= V * 2 + 7 * V * 64 + V * 4  # five kept maps, two gradient maps, loss gradient
+    assert so.muffin_net_workspace_bytes(0, 4, 4, 0) == 0
+    assert so.muffin_net_workspace_bytes(1 << 20, 1 << 10, 1 << 10, 0) == 0
+    assert so.muffin_conv3d_scratch_bytes(3, 5, 7) > 27648 * 2
+    net = ctypes.c_void_p()
+    assert so.muffin_net_create(ctypes.byref(net), 0, 8, 8, 0, None, 0, None) == -1
+    assert so.muffin_net_create(ctypes.byref(net), 4, 8, 8, 0, None, 1 << 20, None) == -1
+    assert so.muffin_net_create(ctypes.byref(net), 4, 8, 8, 0, ctypes.c_void_p(256), 16, None) == -3
+    assert not net.value

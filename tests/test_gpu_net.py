@@ -1,0 +1,174 @@
+"""Warm-start network kernels against the FP64 network oracle.
+
+Inputs and weights are drawn on the bfloat16 grid, so both sides start from
+the same numbers.  A single layer's output then differs from the oracle only by
+float32 accumulation and the final rounding to bfloat16 (half an ulp, 2^-9
+relative); weight gradients are float32 sums of exact products.  Through the
+six layers the bfloat16 roundings of the feature maps add up; the bound used
+there is stated at the test.
+"""
+import numpy as np
+import pytest
+import torch
+
+from oracle import warmstart_net as wn
+from paper_1602_08847_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+
+SHAPES = [(2, 8, 16), (3, 9, 20), (5, 17, 35)]   # one tile; ragged tails along every axis
+
+
+@pytest.fixture(scope="module")
+def netmod(lib):
+    from paper_1602_08847_gb300 import net
+    return net
+
+
+def bf(shape, seed, lo=-1.0, hi=1.0):
+    return synth.bf16_round(synth.random_field(shape, seed, lo, hi).astype(np.float32)).astype(np.float64)
+
+
+def to_map(a):
+    """oracle [C][Z][Y][X] -> device bfloat16 [Z][Y][X][C]."""
+    return torch.from_numpy(np.ascontiguousarray(a.transpose(1, 2, 3, 0)).astype(np.float32)).cuda().to(torch.bfloat16)
+
+
+def from_map(t):
+    return t.float().cpu().numpy().astype(np.float64).transpose(3, 0, 1, 2)
+
+
+def close_bf16(gpu, ref, scale):
+    """Within one bfloat16 ulp of the exact value, plus float32 accumulation."""
+    err = np.abs(gpu - ref)
+    return np.all(err <= 2.0 ** -8 * np.abs(ref) + 1e-5 * scale), float(np.max(err))
+
+
+@pytest.mark.parametrize("shape", SHAPES)
+@pytest.mark.parametrize("relu", [True, False])
+def test_layer_forward(netmod, shape, relu):
+    a = np.maximum(bf((32,) + shape, 1), 0.0)
+    w = bf((32, 32, 3, 3, 3), 2, -0.1, 0.1)
+    b = bf((32,), 3, -0.2, 0.2)
+    ref = wn.conv3d(a, w, b)
+    if relu:
+        ref = np.maximum(ref, 0.0)
+    z = netmod.conv3d_forward(to_map(a), torch.from_numpy(w.astype(np.float32)).cuda(),
+                              torch.from_numpy(b.astype(np.float32)).cuda(), relu)
+    ok, err = close_bf16(from_map(z), ref, np.max(np.abs(ref)))
+    assert ok, err
+
+
+@pytest.mark.parametrize("shape", SHAPES)
+def test_layer_backward_data(netmod, shape):
+    dz = bf((32,) + shape, 4)
+    w = bf((32, 32, 3, 3, 3), 5, -0.1, 0.1)
+    mask = np.maximum(bf((32,) + shape, 6), 0.0)        # a ReLU output: about half zeros
+    da, _, _ = wn.conv3d_backward(np.zeros_like(dz), w, dz)
+    ref = da * (mask > 0)
+    got = netmod.conv3d_backward_data(to_map(dz), torch.from_numpy(w.astype(np.float32)).cuda(), to_map(mask))
+    ok, err = close_bf16(from_map(got), ref, np.max(np.abs(ref)))
+    assert ok, err
+    # without a mask: the plain adjoint
+    got = netmod.conv3d_backward_data(to_map(dz), torch.from_numpy(w.astype(np.float32)).cuda(), None)
+    ok, err = close_bf16(from_map(got), da, np.max(np.abs(da)))
+    assert ok, err
+
+
+@pytest.mark.parametrize("shape", SHAPES + [(8, 40, 64)])
+def test_layer_backward_weights(netmod, shape):
+    a = np.maximum(bf((32,) + shape, 7), 0.0)
+    dz = bf((32,) + shape, 8)
+    _, dw, db = wn.conv3d_backward(a, np.zeros((32, 32, 3, 3, 3)), dz)
+    _, dw_abs, db_abs = wn.conv3d_backward(np.abs(a), np.zeros((32, 32, 3, 3, 3)), np.abs(dz))
+    gdw, gdb = netmod.conv3d_backward_weights(to_map(a), to_map(dz))
+    gdw = gdw.cpu().numpy().astype(np.float64)
+    gdb = gdb.cpu().numpy().astype(np.float64)
+    # float32 sums of exact products: error below n * 2^-24 of the sum of magnitudes
+    n = np.prod(shape)
+    assert np.all(np.abs(gdw - dw) <= n * 2.0 ** -24 * dw_abs + 1e-30)
+    assert np.all(np.abs(gdb - db) <= n * 2.0 ** -24 * db_abs + 1e-30)
+
+
+def net_inputs(shape, seed):
+    """bfloat16-exact dirty cube with max |y| = 1 (so y / s is exact), a target."""
+    y = bf(shape, seed, -0.3, 1.0)
+    y.flat[np.argmax(np.abs(y))] = 1.0
+    t = np.maximum(synth.random_field(shape, seed + 1, -0.5, 1.0), 0.0)
+    return y, t
+
+
+def rel(a, b):
+    return float(np.linalg.norm(a - b) / np.linalg.norm(b))
+
+
+@pytest.mark.parametrize("shape", [(4, 12, 20), (3, 16, 16)])
+def test_network_prediction(netmod, shape):
+    theta = synth.net_init(7).astype(np.float64)
+    y, _ = net_inputs(shape, 11)
+    ref, _, _ = wn.forward(theta, y)
+    ref = np.maximum(ref, 0.0)
+    n = netmod.WarmStartNet(shape, theta=torch.from_numpy(theta.astype(np.float32)).cuda())
+    got = n.predict(torch.from_numpy(y.astype(np.float32)).cuda()).cpu().numpy().astype(np.float64)
+    # five bfloat16 feature maps, each rounded to 2^-9 relative: well inside 2 %
+    assert rel(got, ref) < 2e-2, rel(got, ref)
+    assert np.all(got >= 0)
+
+
+def test_network_loss_and_gradient(netmod):
+    shape = (4, 12, 20)
+    theta = synth.net_init(8).astype(np.float64)
+    theta[-1] = 0.05
+    y, t = net_inputs(shape, 12)
+    loss_ref, g_ref = wn.gradient(theta, y, t)
+    n = netmod.WarmStartNet(shape, training=True, theta=torch.from_numpy(theta.astype(np.float32)).cuda())
+    loss, g = n.loss_grad(torch.from_numpy(y.astype(np.float32)).cuda(), torch.from_numpy(t.astype(np.float32)).cuda())
+    g = g.cpu().numpy().astype(np.float64)
+    assert abs(loss - loss_ref) <= 1e-2 * loss_ref
+    off = 0
+    for ci, co, _ in wn.ARCH:
+        nw = co * ci * 27
+        for part in (slice(off, off + nw), slice(off + nw, off + nw + co)):
+            # bfloat16 feature maps and bfloat16 back-propagated gradients
+            assert rel(g[part], g_ref[part]) < 3e-2, (ci, co, rel(g[part], g_ref[part]))
+            cos = np.dot(g[part], g_ref[part]) / np.linalg.norm(g[part]) / np.linalg.norm(g_ref[part])
+            assert cos > 0.999
+        off += nw + co
+
+
+def test_first_adam_step_moves_by_lr_times_sign(netmod):
+    shape = (2, 8, 16)
+    theta = synth.net_init(9).astype(np.float32)
+    y, t = net_inputs(shape, 13)
+    dev = lambda a: torch.from_numpy(np.ascontiguousarray(a, dtype=np.float32)).cuda()  # noqa: E731
+    n = netmod.WarmStartNet(shape, training=True, theta=dev(theta))
+    _, g = n.loss_grad(dev(y), dev(t))
+    n.train_step(dev(y), dev(t), 1e-3)
+    step = (n.get_params().cpu().numpy() - theta).astype(np.float64)
+    g = g.cpu().numpy().astype(np.float64)
+    big = np.abs(g) > 1e-5
+    assert np.allclose(step[big], -1e-3 * np.sign(g[big]), rtol=1e-3, atol=2e-7)
+
+
+def test_training_lowers_the_loss(netmod):
+    shape = (4, 16, 16)
+    y, _ = net_inputs(shape, 14)
+    t = 0.8 * np.maximum(y, 0.0)                       # learnable from y
+    dev = lambda a: torch.from_numpy(np.ascontiguousarray(a, dtype=np.float32)).cuda()  # noqa: E731
+    n = netmod.WarmStartNet(shape, training=True, theta=dev(synth.net_init(10)))
+    yd, td = dev(y), dev(t)
+    first, _ = n.loss_grad(yd, td)
+    for _ in range(60):
+        n.train_step(yd, td, 2e-3)
+    last, _ = n.loss_grad(yd, td)
+    assert last < 0.5 * first, (first, last)
+
+
+def test_network_argument_errors(netmod):
+    with pytest.raises(ValueError):
+        netmod.WarmStartNet((0, 8, 8))
+    n = netmod.WarmStartNet((2, 8, 8))
+    with pytest.raises(ValueError):
+        n.predict(torch.zeros((2, 8, 9), device="cuda"))
+    with pytest.raises(Exception):
+        n.loss_grad(torch.zeros((2, 8, 8), device="cuda"), torch.zeros((2, 8, 8), device="cuda"))
