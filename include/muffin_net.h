@@ -4,17 +4,21 @@
  *
  * The paper's own warm start is the two-step schedule of Sec. 4: the second
  * run of Algorithm 1 starts from the cube the first run produced.  This
- * network generalises that: trained on (dirty cube, cube after a number of
- * passes of Algorithm 1) pairs, its prediction becomes X of the first pass
- * (muffin_set_cube), and Algorithm 1 runs on from there.  The paper has no
- * network; everything below is defined here.
+ * network generalises that: trained on (dirty cube, state of Algorithm 1
+ * after a number of passes) pairs, it predicts the cube X and, optionally,
+ * the J+1 planes of the wavelet dual U; Algorithm 1 then runs on from the
+ * predicted state (muffin_set_state with V = 0).  The paper has no network;
+ * everything below is defined here.
  *
  * Network: six zero-padded 3x3x3 cross-correlations over (channel, row,
- * column) of the cube, 1 -> 32 -> 32 -> 32 -> 32 -> 32 -> 1 feature maps, a
- * bias and a ReLU after each layer but the last.  Input a0 = y / s with
- * s = max |y| over the dirty cube; prediction max(s * z6, 0).  Loss: mean
- * over voxels of (z6 - t / s)^2 for a target cube t.  Training: Adam (Kingma
- * and Ba, ICLR 2015, Algorithm 1; beta1 0.9, beta2 0.999, eps 1e-8).
+ * column) of the cube, 1 -> 32 -> 32 -> 32 -> 32 -> 32 -> K feature maps
+ * (1 <= K <= 8), a bias and a ReLU after each layer but the last.  Input
+ * a0 = y / s with s = max |y| over the dirty cube.  Outputs: the cube
+ * max(s * z[0], 0) and K-1 fields clamp(z[k], -1, 1), k >= 1.  Loss, for a
+ * target cube t_x, target fields t_aux and output weights lam:
+ *   (1/V) sum_p [lam_0 (z[0] - t_x/s)^2 + sum_{k>=1} lam_k (z[k] - t_aux[k-1])^2].
+ * Training: Adam (Kingma and Ba, ICLR 2015, Algorithm 1; beta1 0.9, beta2
+ * 0.999, eps 1e-8).
  *
  * Arithmetic: weights, activations and activation gradients are bfloat16,
  * every sum is accumulated in float32; master weights, their gradients and
@@ -24,9 +28,10 @@
  * Parameters travel as one packed float32 vector: for each layer in order,
  * its weights [co][ci][3][3][3] (tap index (dz+1)*9 + (dy+1)*3 + (dx+1) for
  * the offset (dz, dy, dx) along (channel, row, column)) and then its biases
- * [co]; 112481 values in all.
+ * [co]; 111616 + 865 K values in all.
  *
- * Cubes: float32 [nz][ny][nx] (nz = spectral channels).  Feature maps:
+ * Cubes: float32 [nz][ny][nx] (nz = spectral channels).  Fields: [nz][K-1]
+ * [ny][nx] (the layout of U in include/muffin.h when K - 1 = J + 1).  Feature maps:
  * bfloat16 [nz][ny][nx][32] (features innermost), passed as void pointers to
  * 16-bit storage.  Pointers named d_* are device pointers, h_* host pointers;
  * the library never allocates: the caller provides workspaces.  Work goes on
@@ -45,41 +50,49 @@ extern "C" {
 
 typedef struct muffin_net muffin_net;
 
-/* Number of packed float32 parameters (112481). */
-int muffin_net_num_params(void);
+/* Number of packed float32 parameters with n_out output maps (0 if n_out is
+ * outside [1, 8]); 112481 for n_out = 1. */
+int muffin_net_num_params(int n_out);
 
-/* Device workspace for a network working on nz x ny x nx cubes; training != 0
- * also holds every activation, the gradients and Adam's moments.  0 if the
- * sizes are invalid (each >= 1, nz*ny*nx < 2^31 / 32). */
-size_t muffin_net_workspace_bytes(int nz, int ny, int nx, int training);
+/* Device workspace for a network with n_out output maps working on
+ * nz x ny x nx cubes; training != 0 also holds every activation, the
+ * gradients and Adam's moments.  0 if the sizes are invalid (each >= 1,
+ * nz*ny*nx < 2^31 / 32, 1 <= n_out <= 8). */
+size_t muffin_net_workspace_bytes(int nz, int ny, int nx, int n_out, int training);
 
 /* Create a network context over a caller-owned workspace (>= the bytes
- * above, 256-byte aligned, valid until muffin_net_destroy).  The parameters
- * start at zero: call muffin_net_set_params. */
-int muffin_net_create(muffin_net** net, int nz, int ny, int nx, int training, void* d_workspace,
-                      size_t ws_bytes, cudaStream_t stream);
+ * above, 256-byte aligned, valid until muffin_net_destroy).  h_out_weight:
+ * host, n_out loss weights lam_k >= 0 (NULL: all 1).  The parameters start
+ * at zero: call muffin_net_set_params. */
+int muffin_net_create(muffin_net** net, int nz, int ny, int nx, int n_out, const float* h_out_weight,
+                      int training, void* d_workspace, size_t ws_bytes, cudaStream_t stream);
 
-/* Load packed float32 parameters (device, 112481 values); resets Adam's
- * moments and step count.  Asynchronous. */
+/* Load packed float32 parameters (device, muffin_net_num_params(n_out)
+ * values); resets Adam's moments and step count.  Asynchronous. */
 int muffin_net_set_params(muffin_net* net, const float* d_theta);
 /* Copy the current packed parameters out (device).  Asynchronous. */
 int muffin_net_get_params(const muffin_net* net, float* d_theta);
 
-/* Prediction of the starting cube: d_x = max(s * net(d_dirty / s), 0), both
- * float32 [nz][ny][nx] on the device.  Asynchronous. */
-int muffin_net_predict(muffin_net* net, const float* d_dirty, float* d_x);
+/* Prediction of the starting state from the dirty cube d_dirty (float32
+ * [nz][ny][nx], device): d_x = max(s * z[0], 0) (float32 [nz][ny][nx]) and,
+ * if n_out > 1, d_aux = clamp(z[k], -1, 1) (float32 [nz][n_out-1][ny][nx];
+ * may be NULL only when n_out == 1).  Asynchronous. */
+int muffin_net_predict(muffin_net* net, const float* d_dirty, float* d_x, float* d_aux);
 
-/* Loss at (d_dirty, d_target) and its packed gradient (device float32,
- * 112481 values), without changing the parameters.  Training contexts only.
- * h_loss (may be NULL) receives the loss; if given, the call synchronises. */
-int muffin_net_loss_grad(muffin_net* net, const float* d_dirty, const float* d_target, float* d_grad,
-                         double* h_loss);
+/* Loss at (d_dirty, d_target_x, d_target_aux) and its packed gradient
+ * (device float32, muffin_net_num_params(n_out) values), without changing
+ * the parameters.  d_target_x: float32 [nz][ny][nx]; d_target_aux: bfloat16
+ * [nz][n_out-1][ny][nx] (NULL only when n_out == 1).  Training contexts only
+ * (else MUFFIN_ERR_STATE).  h_loss (may be NULL) receives the loss; if given,
+ * the call synchronises. */
+int muffin_net_loss_grad(muffin_net* net, const float* d_dirty, const float* d_target_x,
+                         const void* d_target_aux, float* d_grad, double* h_loss);
 
-/* One Adam step on the pair (d_dirty, d_target) at learning rate lr.
- * Training contexts only.  d_loss (device, may be NULL) receives the loss of
- * the pair before the step, as a double.  Asynchronous. */
-int muffin_net_train_step(muffin_net* net, const float* d_dirty, const float* d_target, float lr,
-                          double* d_loss);
+/* One Adam step on the pair at learning rate lr (finite, >= 0).  Training
+ * contexts only.  d_loss (device, may be NULL) receives the loss of the pair
+ * before the step, as a double.  Asynchronous. */
+int muffin_net_train_step(muffin_net* net, const float* d_dirty, const float* d_target_x,
+                          const void* d_target_aux, float lr, double* d_loss);
 
 const char* muffin_net_last_error(const muffin_net* net);  /* net may be NULL (create errors) */
 void muffin_net_destroy(muffin_net* net);

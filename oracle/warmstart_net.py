@@ -13,10 +13,14 @@ module computes has plain definitions, written out below:
   the cube, plus a bias, then ReLU (not after the last layer):
   ``z[co, p] = b[co] + sum_ci sum_{d in {-1,0,1}^3} w[co, ci, d + 1] a[ci, p + d]``
   with ``a[ci, q] = 0`` for q outside the cube;
-* six layers: 1 -> 32 -> 32 -> 32 -> 32 -> 32 -> 1 feature maps;
+* six layers: 1 -> 32 -> 32 -> 32 -> 32 -> 32 -> K feature maps;
 * input normalisation: ``a0 = y / s`` with ``s = max |y|`` over the whole
-  dirty cube; prediction ``s * z6``;
-* loss: mean over voxels of ``(z6 - t / s)^2`` for a target cube t;
+  dirty cube; output map 0 predicts the cube, ``s * z6[0]``; output maps
+  1 .. K-1 predict K-1 further fields of the state of Algorithm 1 (the planes
+  of the wavelet dual U), ``z6[k]`` as they are;
+* loss: ``(1/V) sum_p [lam_0 (z6[0] - t_x / s)^2
+  + sum_{k>=1} lam_k (z6[k] - t_aux[k-1])^2]`` over the V voxels, for a
+  target cube t_x, target fields t_aux and channel weights lam;
 * gradients by the chain rule; the ReLU derivative is 1 where the layer's
   output is > 0 and 0 elsewhere;
 * Adam (Kingma and Ba, "Adam: a method for stochastic optimization", ICLR
@@ -32,7 +36,11 @@ from __future__ import annotations
 import numpy as np
 
 # (input features, output features, ReLU after the layer)
-ARCH = ((1, 32, True), (32, 32, True), (32, 32, True), (32, 32, True), (32, 32, True), (32, 1, False))
+def arch(n_out: int = 1):
+    return ((1, 32, True), (32, 32, True), (32, 32, True), (32, 32, True), (32, 32, True), (32, n_out, False))
+
+
+ARCH = arch(1)
 
 
 def n_params(arch=ARCH) -> int:
@@ -102,10 +110,10 @@ def input_scale(y: np.ndarray) -> float:
 
 
 def forward(theta: np.ndarray, y: np.ndarray, arch=ARCH):
-    """Dirty cube y [L][N][N] -> (prediction [L][N][N], activations, scale s).
+    """Dirty cube y [L][N][N] -> (cube prediction s z6[0] [L][N][N], activations, scale s).
 
     activations[0] is the normalised input, activations[k] the output of layer
-    k (after its ReLU when it has one)."""
+    k (after its ReLU when it has one); activations[6] holds all K output maps."""
     s = input_scale(y)
     a = np.asarray(y, dtype=np.float64)[None] / s
     acts = [a]
@@ -116,19 +124,31 @@ def forward(theta: np.ndarray, y: np.ndarray, arch=ARCH):
     return s * a[0], acts, s
 
 
-def loss(theta: np.ndarray, y: np.ndarray, t: np.ndarray, arch=ARCH) -> float:
+def _residual(acts, s, t, t_aux, lam):
+    """Weighted residual maps r[k] = z6[k] - target[k] and the weights [K]."""
+    z = acts[-1]
+    K = z.shape[0]
+    target = np.empty_like(z)
+    target[0] = np.asarray(t, dtype=np.float64) / s
+    if K > 1:
+        target[1:] = np.asarray(t_aux, dtype=np.float64)
+    lam = np.ones(K) if lam is None else np.asarray(lam, dtype=np.float64)
+    return z - target, lam
+
+
+def loss(theta: np.ndarray, y: np.ndarray, t: np.ndarray, arch=ARCH, t_aux=None, lam=None) -> float:
     _, acts, s = forward(theta, y, arch)
-    r = acts[-1][0] - np.asarray(t, dtype=np.float64) / s
-    return float(np.mean(r * r))
+    r, lam = _residual(acts, s, t, t_aux, lam)
+    return float(np.sum(lam[:, None, None, None] * r * r) / r[0].size)
 
 
-def gradient(theta: np.ndarray, y: np.ndarray, t: np.ndarray, arch=ARCH):
+def gradient(theta: np.ndarray, y: np.ndarray, t: np.ndarray, arch=ARCH, t_aux=None, lam=None):
     """(loss, packed gradient of the loss with respect to theta)."""
     layers = unpack(theta, arch)
     _, acts, s = forward(theta, y, arch)
-    r = acts[-1][0] - np.asarray(t, dtype=np.float64) / s
-    value = float(np.mean(r * r))
-    dz = (2.0 / r.size) * r[None]
+    r, lam = _residual(acts, s, t, t_aux, lam)
+    value = float(np.sum(lam[:, None, None, None] * r * r) / r[0].size)
+    dz = (2.0 / r[0].size) * lam[:, None, None, None] * r
     grads = [None] * len(layers)
     for k in range(len(layers) - 1, -1, -1):
         w, _ = layers[k]

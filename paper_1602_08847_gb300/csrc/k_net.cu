@@ -1,6 +1,8 @@
 // Warm-start network: six zero-padded 3x3x3 convolution layers over the
-// cube (1 -> 32 -> 32 -> 32 -> 32 -> 32 -> 1 feature maps), its loss, its
-// gradients and Adam, all in bfloat16 with float32 accumulation.
+// cube (1 -> 32 -> 32 -> 32 -> 32 -> 32 -> K feature maps, K <= 8), its
+// loss, its gradients and Adam, all in bfloat16 with float32 accumulation.
+// Output map 0 predicts the cube X of Algorithm 1, maps 1 .. K-1 further
+// fields of its state (the planes of the wavelet dual U).
 //
 // Feature maps are [nz][ny][nx][32] bfloat16 (64 bytes per voxel).  Every
 // kernel works on output tiles of 2 x 8 x 16 voxels (channel, row, column)
@@ -19,7 +21,7 @@
 //                 the same kernel on the flipped, transposed weights,
 //   weight grad  dW[tap][co][ci] = sum_p dz[p][co] a[p + d(tap)][ci]
 //                 (M = co, N = ci, K = voxels), one warp per tap.
-// The 1 -> 32 and 32 -> 1 layers are 27 or 864 multiply-adds per voxel and
+// The 1 -> 32 and 32 -> K layers are 27 or 864 multiply-adds per voxel and
 // output; they run on the CUDA cores.  Every reduction over voxels is a
 // per-block partial sum followed by a fixed-order sum: results do not depend
 // on scheduling.
@@ -49,14 +51,11 @@ constexpr int HZ = TZ + 2, HY = TY + 2, HX = TX + 2;
 constexpr int HV = HZ * HY * HX;             // 720 voxels with halo
 constexpr int ROWB = C * 2;                  // 64 bytes per voxel of a map
 constexpr int WMID = NTAP * C * C;           // 27648 weights of a 32 -> 32 layer
-constexpr int NLAYER = 6;
-constexpr int kCi[NLAYER] = {1, 32, 32, 32, 32, 32};
-constexpr int kCo[NLAYER] = {32, 32, 32, 32, 32, 1};
+constexpr int kMaxOut = 8;                   // output maps of the last layer, at most
 constexpr int kMaxPart = 512;                // cap of per-block partial slots (weight gradients)
 constexpr int kMaxLossPart = 1024;
 
 constexpr int conv_smem = NTAP * C * ROWB + HV * ROWB;      // 55296 + 46080
-constexpr int last_smem = HV * ROWB + NTAP * C * 4;         // 46080 + 3456
 
 struct Dims {
   int nz, ny, nx;
@@ -416,26 +415,40 @@ k_first_fwd(const bf16* __restrict__ a0, const float* __restrict__ w, const floa
   }
 }
 
-// z6[p] = b + sum_tap sum_ci a5[p + d(tap)][ci] w[tap][ci].
-// TRAIN = 0: out[p] = max(s z6, 0).  TRAIN = 1: r = z6 - target/s, out[p] =
-// 2 r / V (the loss gradient), lpart[block] = (sum r^2, sum r).
-template <int TRAIN>
+// Per-output-map constants of the last layer (at most kMaxOut maps), by value.
+struct Lam {
+  float v[kMaxOut];
+};
+
+// Last layer, K output maps: z[k][p] = b[k] + sum_tap sum_ci a5[p + d(tap)][ci] w[tap][ci][k].
+// TRAIN = 0 (prediction): out_x[p] = max(s z[0][p], 0) and, for k >= 1,
+//   out_aux[z][k-1][y][x] = clamp(z[k][p], -1, 1) (the dual fields of Algorithm 1 lie in [-1, 1]).
+// TRAIN = 1 (loss): r0 = z[0] - tx / s, rk = z[k] - taux[z][k-1][y][x];
+//   d6[p][k] = 2 lam_k rk / V (the loss gradient of z[k]);
+//   lpart[block] = (sum_k lam_k sum_p rk^2, sum_p r0, ..., sum_p r_{K-1}).
+template <int TRAIN, int K>
 __global__ void __launch_bounds__(256)
 k_last_fwd(const bf16* __restrict__ a5, const float* __restrict__ w, const float* __restrict__ b,
-           const float* __restrict__ target, const float* __restrict__ s_ptr, float* __restrict__ out,
+           const float* __restrict__ tx, const bf16* __restrict__ taux, Lam lam, const float* __restrict__ s_ptr,
+           float* __restrict__ out_x, float* __restrict__ out_aux, float* __restrict__ d6,
            double* __restrict__ lpart, Dims d) {
   extern __shared__ __align__(128) unsigned char smem[];
   const uint32_t s_a = smem_u32(smem);
-  float* s_w = reinterpret_cast<float*>(smem + HV * ROWB);
+  float* s_w = reinterpret_cast<float*>(smem + HV * ROWB);   // [27][32][K]
   __shared__ double s_red[32];
-  for (int i = threadIdx.x; i < NTAP * C; i += blockDim.x) s_w[i] = w[i];
-  const float bias = b[0];
+  for (int i = threadIdx.x; i < NTAP * C * K; i += blockDim.x) s_w[i] = w[i];
+  float bias[K];
+#pragma unroll
+  for (int k = 0; k < K; ++k) bias[k] = b[k];
   const float s = *s_ptr;
   const float inv_s = 1.0f / s;
-  const float gscale = (float)(2.0 / (double)d.nvox);
-  int tz, ty, tx;
-  thread_voxel(tz, ty, tx);
-  double l2 = 0.0, l1 = 0.0;
+  const size_t plane = (size_t)d.ny * d.nx;
+  int tz, ty, tx_;
+  thread_voxel(tz, ty, tx_);
+  double l2 = 0.0;
+  double lsum[K];
+#pragma unroll
+  for (int k = 0; k < K; ++k) lsum[k] = 0.0;
   for (int tile = blockIdx.x; tile < d.ntiles; tile += gridDim.x) {
     int z0, y0, x0;
     tile_origin(tile, d, z0, y0, x0);
@@ -443,11 +456,13 @@ k_last_fwd(const bf16* __restrict__ a5, const float* __restrict__ w, const float
     load_map_halo<HZ>(s_a, a5, d, z0 - 1, y0, x0);
     cp_async_wait_all();
     __syncthreads();
-    float acc = bias;
+    float acc[K];
+#pragma unroll
+    for (int k = 0; k < K; ++k) acc[k] = bias[k];
 #pragma unroll 1
     for (int t = 0; t < NTAP; ++t) {
       const int kz = t / 9, ky = (t / 3) % 3, kx = t % 3;
-      const int h = ((tz + kz) * HY + ty + ky) * HX + tx + kx;
+      const int h = ((tz + kz) * HY + ty + ky) * HX + tx_ + kx;
 #pragma unroll
       for (int c = 0; c < 4; ++c) {
         uint4 q;
@@ -455,48 +470,67 @@ k_last_fwd(const bf16* __restrict__ a5, const float* __restrict__ w, const float
                      : "=r"(q.x), "=r"(q.y), "=r"(q.z), "=r"(q.w) : "r"(s_a + swz(h, c)));
         float f[8];
         unpack8(q, f);
+        const float* wr = s_w + (t * C + c * 8) * K;
 #pragma unroll
-        for (int e = 0; e < 8; ++e) acc = fmaf(f[e], s_w[t * C + c * 8 + e], acc);
+        for (int e = 0; e < 8; ++e)
+#pragma unroll
+          for (int k = 0; k < K; ++k) acc[k] = fmaf(f[e], wr[e * K + k], acc[k]);
       }
     }
-    const int z = z0 + tz, y = y0 + ty, x = x0 + tx;
+    const int z = z0 + tz, y = y0 + ty, x = x0 + tx_;
     if (inside(d, z, y, x)) {
       const size_t v = vox(d, z, y, x);
+      const size_t a0 = ((size_t)z * (K > 1 ? K - 1 : 1)) * plane + (size_t)y * d.nx + x;
       if (TRAIN) {
-        const float r = acc - target[v] * inv_s;
-        out[v] = gscale * r;
-        l2 += (double)r * r;
-        l1 += r;
+        const double gs = 2.0 / (double)d.nvox;
+#pragma unroll
+        for (int k = 0; k < K; ++k) {
+          const float tk = k == 0 ? tx[v] * inv_s : __bfloat162float(taux[a0 + (size_t)(k - 1) * plane]);
+          const float r = acc[k] - tk;
+          d6[v * K + k] = (float)(gs * lam.v[k]) * r;
+          l2 += (double)lam.v[k] * r * r;
+          lsum[k] += r;
+        }
       } else {
-        out[v] = fmaxf(s * acc, 0.f);
+        out_x[v] = fmaxf(s * acc[0], 0.f);
+#pragma unroll
+        for (int k = 1; k < K; ++k) out_aux[a0 + (size_t)(k - 1) * plane] = fminf(fmaxf(acc[k], -1.f), 1.f);
       }
     }
   }
   if (TRAIN) {
     const double t2 = muffin::block_sum(l2, s_red);
-    __syncthreads();
-    const double t1 = muffin::block_sum(l1, s_red);
-    if (threadIdx.x == 0) {
-      lpart[2 * blockIdx.x] = t2;
-      lpart[2 * blockIdx.x + 1] = t1;
+    if (threadIdx.x == 0) lpart[(size_t)blockIdx.x * (K + 1)] = t2;
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+      __syncthreads();
+      const double tk = muffin::block_sum(lsum[k], s_red);
+      if (threadIdx.x == 0) lpart[(size_t)blockIdx.x * (K + 1) + 1 + k] = tk;
     }
   }
 }
 
-// g5[p][ci] = (a5[p][ci] > 0) * sum_tap d6[p - d(tap)] w[tap][ci].
+// g5[p][ci] = (a5[p][ci] > 0) * sum_tap sum_k d6[p - d(tap)][k] w[tap][k][ci].
+template <int K>
 __global__ void __launch_bounds__(256)
 k_last_bwd_data(const float* __restrict__ d6, const float* __restrict__ w, const bf16* __restrict__ a5,
                 bf16* __restrict__ g5, Dims d) {
-  __shared__ __align__(16) float s_w[NTAP * C];
-  __shared__ float s_h[HV];
-  for (int i = threadIdx.x; i < NTAP * C; i += blockDim.x) s_w[i] = w[i];
+  extern __shared__ __align__(16) float smf[];
+  float* s_w = smf;                      // [27][K][32]
+  float* s_h = smf + NTAP * K * C;       // [HV][K]
+  for (int i = threadIdx.x; i < NTAP * K * C; i += blockDim.x) s_w[i] = w[i];
   int tz, ty, tx;
   thread_voxel(tz, ty, tx);
   for (int tile = blockIdx.x; tile < d.ntiles; tile += gridDim.x) {
     int z0, y0, x0;
     tile_origin(tile, d, z0, y0, x0);
     __syncthreads();
-    load_scalar_halo(s_h, d6, d, z0, y0, x0);
+    for (int i = threadIdx.x; i < HV * K; i += blockDim.x) {
+      const int h = i / K, k = i - h * K;
+      const int hx = h % HX, r = h / HX, hy = r % HY, hz = r / HY;
+      const int gz = z0 - 1 + hz, gy = y0 - 1 + hy, gx = x0 - 1 + hx;
+      s_h[i] = inside(d, gz, gy, gx) ? d6[vox(d, gz, gy, gx) * K + k] : 0.f;
+    }
     __syncthreads();
     float acc[C];
 #pragma unroll
@@ -504,15 +538,19 @@ k_last_bwd_data(const float* __restrict__ d6, const float* __restrict__ w, const
 #pragma unroll 1
     for (int t = 0; t < NTAP; ++t) {
       const int kz = t / 9, ky = (t / 3) % 3, kx = t % 3;
-      const float dv = s_h[((tz + 2 - kz) * HY + ty + 2 - ky) * HX + tx + 2 - kx];
-      const float4* wr = reinterpret_cast<const float4*>(s_w + t * C);
+      const int hh = ((tz + 2 - kz) * HY + ty + 2 - ky) * HX + tx + 2 - kx;
 #pragma unroll
-      for (int q = 0; q < C / 4; ++q) {
-        const float4 wv = wr[q];
-        acc[4 * q] = fmaf(dv, wv.x, acc[4 * q]);
-        acc[4 * q + 1] = fmaf(dv, wv.y, acc[4 * q + 1]);
-        acc[4 * q + 2] = fmaf(dv, wv.z, acc[4 * q + 2]);
-        acc[4 * q + 3] = fmaf(dv, wv.w, acc[4 * q + 3]);
+      for (int k = 0; k < K; ++k) {
+        const float dv = s_h[hh * K + k];
+        const float4* wr = reinterpret_cast<const float4*>(s_w + (t * K + k) * C);
+#pragma unroll
+        for (int q = 0; q < C / 4; ++q) {
+          const float4 wv = wr[q];
+          acc[4 * q] = fmaf(dv, wv.x, acc[4 * q]);
+          acc[4 * q + 1] = fmaf(dv, wv.y, acc[4 * q + 1]);
+          acc[4 * q + 2] = fmaf(dv, wv.z, acc[4 * q + 2]);
+          acc[4 * q + 3] = fmaf(dv, wv.w, acc[4 * q + 3]);
+        }
       }
     }
     const int z = z0 + tz, y = y0 + ty, x = x0 + tx;
@@ -570,35 +608,43 @@ k_wgrad_first(const bf16* __restrict__ a0, const bf16* __restrict__ g1, float* _
   if (t == 0) bpart[(size_t)blockIdx.x * C + co] = bacc;
 }
 
-// part[b][tap][ci] = sum_p d6[p] a5[p + d(tap)][ci].  864 threads: thread (tap, ci).
+
+// part[b][tap][ci][k] = sum_p d6[p][k] a5[p + d(tap)][ci].  864 threads: thread (tap, ci).
+template <int K>
 __global__ void __launch_bounds__(864)
 k_wgrad_last(const float* __restrict__ d6, const bf16* __restrict__ a5, float* __restrict__ part, Dims d) {
-  __shared__ __align__(128) unsigned char s_a[HV * ROWB];
-  __shared__ float s_d[TV];
-  const uint32_t sa = smem_u32(s_a);
+  extern __shared__ __align__(128) unsigned char smem[];
+  const uint32_t sa = smem_u32(smem);
+  float* s_d = reinterpret_cast<float*>(smem + HV * ROWB);   // [TV][K]
   const int t = threadIdx.x >> 5, ci = threadIdx.x & 31;
   const int kz = t / 9, ky = (t / 3) % 3, kx = t % 3;
-  float acc = 0.f;
+  float acc[K];
+#pragma unroll
+  for (int k = 0; k < K; ++k) acc[k] = 0.f;
   for (int tile = blockIdx.x; tile < d.ntiles; tile += gridDim.x) {
     int z0, y0, x0;
     tile_origin(tile, d, z0, y0, x0);
     __syncthreads();
     load_map_halo<HZ>(sa, a5, d, z0 - 1, y0, x0);
-    for (int r = threadIdx.x; r < TV; r += blockDim.x) {
+    for (int i = threadIdx.x; i < TV * K; i += blockDim.x) {
+      const int r = i / K, k = i - r * K;
       const int gz = z0 + (r >> 7), gy = y0 + ((r >> 4) & 7), gx = x0 + (r & 15);
-      s_d[r] = inside(d, gz, gy, gx) ? d6[vox(d, gz, gy, gx)] : 0.f;
+      s_d[i] = inside(d, gz, gy, gx) ? d6[vox(d, gz, gy, gx) * K + k] : 0.f;
     }
     cp_async_wait_all();
     __syncthreads();
-#pragma unroll 4
+#pragma unroll 2
     for (int v = 0; v < TV; ++v) {
       const int vtx = v & 15, vty = (v >> 4) & 7, vtz = v >> 7;
       const int h = ((vtz + kz) * HY + vty + ky) * HX + vtx + kx;
-      const float av = __bfloat162float(*reinterpret_cast<const bf16*>(s_a + swz(h, ci >> 3) + (ci & 7) * 2));
-      acc = fmaf(s_d[v], av, acc);
+      const float av = __bfloat162float(*reinterpret_cast<const bf16*>(smem + swz(h, ci >> 3) + (ci & 7) * 2));
+#pragma unroll
+      for (int k = 0; k < K; ++k) acc[k] = fmaf(s_d[v * K + k], av, acc[k]);
     }
   }
-  part[(size_t)blockIdx.x * (NTAP * C) + t * C + ci] = acc;
+  float* pp = part + ((size_t)blockIdx.x * (NTAP * C) + t * C + ci) * K;
+#pragma unroll
+  for (int k = 0; k < K; ++k) pp[k] = acc[k];
 }
 
 // ------------------------------------------------------------------ reductions, input, parameters
@@ -607,8 +653,8 @@ enum { MAP_PLAIN = 0, MAP_MID = 1, MAP_FIRST = 2, MAP_LAST = 3 };
 
 // out[map(i)] = sum_b part[b*n + i] (fixed order, double accumulation).
 // MAP_MID: i = (tap*32 + co)*32 + ci -> (co*32 + ci)*27 + tap; MAP_FIRST:
-// i = tap*32 + co -> co*27 + tap; MAP_LAST: i = tap*32 + ci -> ci*27 + tap.
-__global__ void k_reduce_part(const float* __restrict__ part, int P, int n, float* __restrict__ out, int map) {
+// i = tap*32 + co -> co*27 + tap; MAP_LAST: i = (tap*32 + ci)*K + k -> (k*32 + ci)*27 + tap.
+__global__ void k_reduce_part(const float* __restrict__ part, int P, int n, float* __restrict__ out, int map, int K) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
   double s = 0.0;
@@ -617,24 +663,29 @@ __global__ void k_reduce_part(const float* __restrict__ part, int P, int n, floa
   if (map == MAP_MID) {
     const int t = i >> 10, co = (i >> 5) & 31, ci = i & 31;
     j = (co * C + ci) * NTAP + t;
-  } else if (map == MAP_FIRST || map == MAP_LAST) {
+  } else if (map == MAP_FIRST) {
     const int t = i >> 5, c = i & 31;
     j = c * NTAP + t;
+  } else if (map == MAP_LAST) {
+    const int k = i % K, r = i / K, ci = r & 31, t = r >> 5;
+    j = (k * C + ci) * NTAP + t;
   }
   out[j] = (float)s;
 }
 
-// loss = sum r^2 / V; gradient of the last bias = 2 sum r / V.
-__global__ void k_loss_final(const double* __restrict__ lpart, int P, long long nvox, double* __restrict__ loss,
-                             float* __restrict__ grad_b6) {
-  if (threadIdx.x != 0 || blockIdx.x != 0) return;
-  double l2 = 0.0, l1 = 0.0;
-  for (int b = 0; b < P; ++b) {
-    l2 += lpart[2 * b];
-    l1 += lpart[2 * b + 1];
+// loss = sum_b lpart[b][0] / V; gradient of the last biases: 2 lam_k sum_b lpart[b][1+k] / V.
+__global__ void k_loss_final(const double* __restrict__ lpart, int P, int K, Lam lam, long long nvox,
+                             double* __restrict__ loss, float* __restrict__ grad_b6) {
+  if (blockIdx.x != 0) return;
+  const int k = (int)threadIdx.x - 1;
+  if (k >= K) return;
+  double acc = 0.0;
+  for (int b = 0; b < P; ++b) acc += lpart[(size_t)b * (K + 1) + 1 + k];
+  if (k < 0) {
+    if (loss) *loss = acc / (double)nvox;
+  } else if (grad_b6) {
+    grad_b6[k] = (float)(2.0 * lam.v[k] * acc / (double)nvox);
   }
-  if (loss) *loss = l2 / (double)nvox;
-  if (grad_b6) *grad_b6 = (float)(2.0 * l1 / (double)nvox);
 }
 
 __global__ void k_maxabs_part(const float* __restrict__ y, long long n, float* __restrict__ part) {
@@ -653,7 +704,7 @@ __global__ void k_maxabs_part(const float* __restrict__ y, long long n, float* _
   }
 }
 
-// s = max |y| (1 if the cube is zero); a0 = bf16(y / s).
+// s = max |y| (1 if the cube is zero).
 __global__ void k_scale_final(const float* __restrict__ part, int P, float* __restrict__ s) {
   if (threadIdx.x != 0 || blockIdx.x != 0) return;
   float m = 0.f;
@@ -661,6 +712,7 @@ __global__ void k_scale_final(const float* __restrict__ part, int P, float* __re
   *s = m > 0.f ? m : 1.f;
 }
 
+// a0 = bf16(y / s).
 __global__ void k_prep_input(const float* __restrict__ y, const float* __restrict__ s, bf16* __restrict__ a0,
                              long long n) {
   const float inv = 1.0f / *s;
@@ -674,18 +726,19 @@ struct KernelWeights {
   bf16* wf;     // [4][27][32 co][32 ci]   forward operands of layers 2..5
   bf16* wb;     // [4][27][32 ci][32 co]   flipped, transposed: input gradients
   float* bm;    // [4][32]
-  float* w6;    // [27][32] (tap, ci), bfloat16 values
-  float* b6;    // [1]
+  float* w6f;   // [27][32 ci][K]  last layer, forward; bfloat16 values
+  float* w6b;   // [27][K][32 ci]  last layer, input gradient
+  float* b6;    // [K]
 };
 
 __device__ __forceinline__ float round_bf16(float v) { return __bfloat162float(__float2bfloat16_rn(v)); }
 
 // Packed float32 parameters -> the layouts the kernels read.
-__global__ void k_unpack_params(const float* __restrict__ theta, KernelWeights kw) {
+__global__ void k_unpack_params(const float* __restrict__ theta, KernelWeights kw, int K) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   constexpr int L1 = NTAP * C + C;           // 896
   constexpr int LM = WMID + C;               // 27680
-  constexpr int N = L1 + 4 * LM + NTAP * C + 1;
+  const int N = L1 + 4 * LM + K * NTAP * C + K;
   if (i >= N) return;
   const float v = theta[i];
   if (i < L1) {
@@ -707,8 +760,14 @@ __global__ void k_unpack_params(const float* __restrict__ theta, KernelWeights k
     return;
   }
   j -= 4 * LM;
-  if (j < NTAP * C) kw.w6[(j % NTAP) * C + j / NTAP] = round_bf16(v);
-  else kw.b6[0] = v;
+  if (j < K * NTAP * C) {
+    const int k = j / (C * NTAP), rem = j % (C * NTAP), ci = rem / NTAP, t = rem % NTAP;
+    const float r = round_bf16(v);
+    kw.w6f[(t * C + ci) * K + k] = r;
+    kw.w6b[(t * K + k) * C + ci] = r;
+  } else {
+    kw.b6[j - K * NTAP * C] = v;
+  }
 }
 
 // One 32 -> 32 layer's weights [co][ci][27] float32 -> forward ([27][co][ci])
@@ -737,18 +796,18 @@ __global__ void k_adam(float* __restrict__ theta, const float* __restrict__ g, f
 
 // ------------------------------------------------------------------ host side
 
-int param_count() {
-  int n = 0;
-  for (int k = 0; k < NLAYER; ++k) n += kCo[k] * kCi[k] * NTAP + kCo[k];
-  return n;
-}
+constexpr int kFixedParams = NTAP * C + C + 4 * (WMID + C);   // layers 1..5
 
-int w_offset(int k) {  // packed offset of layer k's weights
-  int n = 0;
-  for (int j = 0; j < k; ++j) n += kCo[j] * kCi[j] * NTAP + kCo[j];
-  return n;
+int param_count(int K) { return kFixedParams + K * (NTAP * C + 1); }
+
+int w_offset(int k) {  // packed offset of layer k's weights (k = 0..5)
+  if (k == 0) return 0;
+  return NTAP * C + C + (k - 1) * (WMID + C);
 }
-int b_offset(int k) { return w_offset(k) + kCo[k] * kCi[k] * NTAP; }
+int b_offset(int k, int K) {
+  const int co = k == 5 ? K : C, ci = k == 0 ? 1 : C;
+  return w_offset(k) + co * ci * NTAP;
+}
 
 inline size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 
@@ -768,17 +827,50 @@ int sm_count() {
   return n;
 }
 
-cudaError_t configure_once() {
-  static bool done = false;
-  static cudaError_t err = cudaSuccess;
-  if (done) return err;
-  done = true;
-  if ((err = muffin::allow_max_dyn_smem(k_conv_tc<EPI_RELU>)) != cudaSuccess) return err;
-  if ((err = muffin::allow_max_dyn_smem(k_conv_tc<EPI_BIAS>)) != cudaSuccess) return err;
-  if ((err = muffin::allow_max_dyn_smem(k_conv_tc<EPI_MASK>)) != cudaSuccess) return err;
-  if ((err = muffin::allow_max_dyn_smem(k_last_fwd<0>)) != cudaSuccess) return err;
-  err = muffin::allow_max_dyn_smem(k_last_fwd<1>);
-  return err;
+constexpr int last_fwd_smem(int K) { return HV * ROWB + NTAP * C * K * 4; }
+constexpr int last_bwd_smem(int K) { return K * (NTAP * C + HV) * 4; }
+constexpr int wgrad_last_smem(int K) { return HV * ROWB + TV * K * 4; }
+
+template <int K>
+cudaError_t configure_last() {
+  cudaError_t e;
+  if ((e = muffin::allow_max_dyn_smem(k_last_fwd<0, K>)) != cudaSuccess) return e;
+  if ((e = muffin::allow_max_dyn_smem(k_last_fwd<1, K>)) != cudaSuccess) return e;
+  if ((e = muffin::allow_max_dyn_smem(k_last_bwd_data<K>)) != cudaSuccess) return e;
+  return muffin::allow_max_dyn_smem(k_wgrad_last<K>);
+}
+
+#define MNET_SWITCH_K(K, EXPR)     \
+  switch (K) {                     \
+    case 1: { constexpr int KK = 1; EXPR; } break; \
+    case 2: { constexpr int KK = 2; EXPR; } break; \
+    case 3: { constexpr int KK = 3; EXPR; } break; \
+    case 4: { constexpr int KK = 4; EXPR; } break; \
+    case 5: { constexpr int KK = 5; EXPR; } break; \
+    case 6: { constexpr int KK = 6; EXPR; } break; \
+    case 7: { constexpr int KK = 7; EXPR; } break; \
+    case 8: { constexpr int KK = 8; EXPR; } break; \
+    default: break;                \
+  }
+
+cudaError_t configure_once(int K) {
+  static bool mid_done = false;
+  static cudaError_t mid_err = cudaSuccess;
+  static bool last_done[kMaxOut + 1] = {};
+  static cudaError_t last_err[kMaxOut + 1] = {};
+  if (!mid_done) {
+    mid_done = true;
+    if ((mid_err = muffin::allow_max_dyn_smem(k_conv_tc<EPI_RELU>)) == cudaSuccess &&
+        (mid_err = muffin::allow_max_dyn_smem(k_conv_tc<EPI_BIAS>)) == cudaSuccess)
+      mid_err = muffin::allow_max_dyn_smem(k_conv_tc<EPI_MASK>);
+  }
+  if (mid_err != cudaSuccess) return mid_err;
+  if (K < 1 || K > kMaxOut) return cudaSuccess;
+  if (!last_done[K]) {
+    last_done[K] = true;
+    MNET_SWITCH_K(K, last_err[K] = configure_last<KK>());
+  }
+  return last_err[K];
 }
 
 // Launch helpers (all persistent: grids bounded by the tile count).
@@ -795,8 +887,8 @@ void launch_wgrad_mid(const bf16* a, const bf16* dz, float* part, float* bpart, 
   int P = part_slots(d);
   if (P > sms) P = sms;
   k_wgrad_tc<<<dim3(P, 3), 288, 0, st>>>(a, dz, part, bpart, d);
-  k_reduce_part<<<(WMID + 255) / 256, 256, 0, st>>>(part, P, WMID, dw, MAP_MID);
-  if (db) k_reduce_part<<<1, 32, 0, st>>>(bpart, P, C, db, MAP_PLAIN);
+  k_reduce_part<<<(WMID + 255) / 256, 256, 0, st>>>(part, P, WMID, dw, MAP_MID, 1);
+  if (db) k_reduce_part<<<1, 32, 0, st>>>(bpart, P, C, db, MAP_PLAIN, 1);
 }
 
 }  // namespace mnet
@@ -807,6 +899,8 @@ using namespace mnet;
 
 struct muffin_net {
   int training = 0;
+  int K = 1;          // output maps
+  Lam lam{};
   Dims d{};
   cudaStream_t st = nullptr;
   int sms = 148;
@@ -827,7 +921,7 @@ struct muffin_net {
   bf16* act = nullptr;   // training: a1..a5; inference: two ping-pong maps
   bf16* gA = nullptr;
   bf16* gB = nullptr;
-  float* d6 = nullptr;
+  float* d6 = nullptr;   // [V][K]
 
   bf16* map(int i) const { return act + (size_t)i * d.nvox * C; }
 };
@@ -835,14 +929,14 @@ struct muffin_net {
 namespace {
 
 // Workspace carve-up; with base == nullptr only the size is computed.
-size_t net_layout(muffin_net* n, const Dims& d, int training, char* base) {
+size_t net_layout(muffin_net* n, const Dims& d, int K, int training, char* base) {
   size_t off = 0;
   auto take = [&](size_t bytes) -> char* {
     char* p = base ? base + off : nullptr;
     off = align256(off + bytes);
     return p;
   };
-  const int np = param_count();
+  const int np = param_count(K);
   const size_t V = (size_t)d.nvox;
   float* theta = (float*)take(np * 4);
   float* m1 = (float*)take(training ? np * 4 : 0);
@@ -854,11 +948,12 @@ size_t net_layout(muffin_net* n, const Dims& d, int training, char* base) {
   kw.wf = (bf16*)take(4 * WMID * 2);
   kw.wb = (bf16*)take(4 * WMID * 2);
   kw.bm = (float*)take(4 * C * 4);
-  kw.w6 = (float*)take(NTAP * C * 4);
-  kw.b6 = (float*)take(4);
+  kw.w6f = (float*)take(NTAP * C * K * 4);
+  kw.w6b = (float*)take(NTAP * C * K * 4);
+  kw.b6 = (float*)take(K * 4);
   float* s = (float*)take(4);
   float* mpart = (float*)take(kMaxLossPart * 4);
-  double* lpart = (double*)take(2 * kMaxLossPart * 8);
+  double* lpart = (double*)take((size_t)(K + 1) * kMaxLossPart * 8);
   double* loss = (double*)take(8);
   const int P = part_slots(d);
   float* part = (float*)take(training ? (size_t)P * WMID * 4 : 0);
@@ -867,7 +962,7 @@ size_t net_layout(muffin_net* n, const Dims& d, int training, char* base) {
   bf16* act = (bf16*)take((training ? 5 : 2) * V * C * 2);
   bf16* gA = (bf16*)take(training ? V * C * 2 : 0);
   bf16* gB = (bf16*)take(training ? V * C * 2 : 0);
-  float* d6 = (float*)take(training ? V * 4 : 0);
+  float* d6 = (float*)take(training ? V * K * 4 : 0);
   if (n) {
     n->theta = theta; n->mom1 = m1; n->mom2 = m2; n->grad = grad; n->kw = kw;
     n->s = s; n->mpart = mpart; n->lpart = lpart; n->loss = loss; n->part = part; n->bpart = bpart;
@@ -908,68 +1003,98 @@ void forward_to_a5(muffin_net* n, const float* y) {
 
 bf16* a5_of(muffin_net* n) { return n->training ? n->map(4) : n->map(0); }
 
-// Loss and gradient into n->grad (training contexts).
-void loss_and_grad(muffin_net* n, const float* y, const float* t) {
+template <int K>
+void last_predict(muffin_net* n, float* x, float* aux) {
+  const int PL = loss_slots(n->d);
+  k_last_fwd<0, K><<<PL, 256, last_fwd_smem(K), n->st>>>(a5_of(n), n->kw.w6f, n->kw.b6, nullptr, nullptr, n->lam,
+                                                           n->s, x, aux, nullptr, nullptr, n->d);
+}
+
+// Last layer of the training pass: loss, d6, its weight and bias gradients,
+// and the gradient of a5's pre-activation into g5.
+template <int K>
+void last_train(muffin_net* n, const float* tx, const bf16* taux, bf16* g5) {
   const Dims& d = n->d;
-  forward_to_a5(n, y);
   bf16* a5 = a5_of(n);
   const int PL = loss_slots(d);
-  k_last_fwd<1><<<PL, 256, last_smem, n->st>>>(a5, n->kw.w6, n->kw.b6, t, n->s, n->d6, n->lpart, d);
-  k_loss_final<<<1, 32, 0, n->st>>>(n->lpart, PL, d.nvox, n->loss, n->grad + b_offset(5));
+  k_last_fwd<1, K><<<PL, 256, last_fwd_smem(K), n->st>>>(a5, n->kw.w6f, n->kw.b6, tx, taux, n->lam, n->s, nullptr,
+                                                           nullptr, n->d6, n->lpart, d);
+  k_loss_final<<<1, K + 1, 0, n->st>>>(n->lpart, PL, K, n->lam, d.nvox, n->loss, n->grad + b_offset(5, K));
   int P = part_slots(d);
   if (P > 2 * n->sms) P = 2 * n->sms;
-  k_wgrad_last<<<P, 864, 0, n->st>>>(n->d6, a5, n->part, d);
-  k_reduce_part<<<(NTAP * C + 255) / 256, 256, 0, n->st>>>(n->part, P, NTAP * C, n->grad + w_offset(5), MAP_LAST);
+  k_wgrad_last<K><<<P, 864, wgrad_last_smem(K), n->st>>>(n->d6, a5, n->part, d);
+  k_reduce_part<<<(NTAP * C * K + 255) / 256, 256, 0, n->st>>>(n->part, P, NTAP * C * K, n->grad + w_offset(5),
+                                                               MAP_LAST, K);
   const int gsimt = d.ntiles < 4 * n->sms ? d.ntiles : 4 * n->sms;
+  k_last_bwd_data<K><<<gsimt, 256, last_bwd_smem(K), n->st>>>(n->d6, n->kw.w6b, a5, g5, d);
+}
+
+// Loss and gradient into n->grad (training contexts).
+void loss_and_grad(muffin_net* n, const float* y, const float* tx, const bf16* taux) {
+  const Dims& d = n->d;
+  forward_to_a5(n, y);
   bf16* g = n->gA;
   bf16* other = n->gB;
-  k_last_bwd_data<<<gsimt, 256, 0, n->st>>>(n->d6, n->kw.w6, a5, g, d);
+  MNET_SWITCH_K(n->K, last_train<KK>(n, tx, taux, g));
   for (int k = 4; k >= 1; --k) {          // layers 5..2 (index k), input map a_k = map(k - 1)
     const bf16* a_in = n->map(k - 1);
-    launch_wgrad_mid(a_in, g, n->part, n->bpart, n->grad + w_offset(k), n->grad + b_offset(k), d, n->sms, n->st);
+    launch_wgrad_mid(a_in, g, n->part, n->bpart, n->grad + w_offset(k), n->grad + b_offset(k, n->K), d, n->sms,
+                     n->st);
     launch_conv(EPI_MASK, g, n->kw.wb + (size_t)(k - 1) * WMID, nullptr, a_in, other, d, n->sms, n->st);
     bf16* tmp = g; g = other; other = tmp;
   }
-  P = part_slots(d);
+  int P = part_slots(d);
   if (P > 2 * n->sms) P = 2 * n->sms;
   k_wgrad_first<<<P, 864, 0, n->st>>>(n->a0, g, n->part, n->bpart, d);
-  k_reduce_part<<<(NTAP * C + 255) / 256, 256, 0, n->st>>>(n->part, P, NTAP * C, n->grad + w_offset(0), MAP_FIRST);
-  k_reduce_part<<<1, 32, 0, n->st>>>(n->bpart, P, C, n->grad + b_offset(0), MAP_PLAIN);
+  k_reduce_part<<<(NTAP * C + 255) / 256, 256, 0, n->st>>>(n->part, P, NTAP * C, n->grad + w_offset(0), MAP_FIRST, 1);
+  k_reduce_part<<<1, 32, 0, n->st>>>(n->bpart, P, C, n->grad + b_offset(0, n->K), MAP_PLAIN, 1);
 }
 
 void unpack_params(muffin_net* n) {
-  const int np = param_count();
-  k_unpack_params<<<(np + 255) / 256, 256, 0, n->st>>>(n->theta, n->kw);
+  const int np = param_count(n->K);
+  k_unpack_params<<<(np + 255) / 256, 256, 0, n->st>>>(n->theta, n->kw, n->K);
 }
 
 }  // namespace
 
 extern "C" {
 
-int muffin_net_num_params(void) { return param_count(); }
-
-size_t muffin_net_workspace_bytes(int nz, int ny, int nx, int training) {
-  if (!dims_ok(nz, ny, nx)) return 0;
-  return net_layout(nullptr, make_dims(nz, ny, nx), training != 0, nullptr);
+int muffin_net_num_params(int n_out) {
+  if (n_out < 1 || n_out > kMaxOut) return 0;
+  return param_count(n_out);
 }
 
-int muffin_net_create(muffin_net** out, int nz, int ny, int nx, int training, void* d_ws, size_t ws_bytes,
-                      cudaStream_t stream) {
+size_t muffin_net_workspace_bytes(int nz, int ny, int nx, int n_out, int training) {
+  if (!dims_ok(nz, ny, nx) || n_out < 1 || n_out > kMaxOut) return 0;
+  return net_layout(nullptr, make_dims(nz, ny, nx), n_out, training != 0, nullptr);
+}
+
+int muffin_net_create(muffin_net** out, int nz, int ny, int nx, int n_out, const float* h_out_weight, int training,
+                      void* d_ws, size_t ws_bytes, cudaStream_t stream) {
   if (!out) return MUFFIN_ERR_ARG;
   *out = nullptr;
-  if (!dims_ok(nz, ny, nx)) return MUFFIN_ERR_ARG;
+  if (!dims_ok(nz, ny, nx) || n_out < 1 || n_out > kMaxOut) return MUFFIN_ERR_ARG;
+  Lam lam;
+  for (int k = 0; k < kMaxOut; ++k) lam.v[k] = 1.f;
+  if (h_out_weight)
+    for (int k = 0; k < n_out; ++k) {
+      if (!(h_out_weight[k] >= 0.f) || !std::isfinite(h_out_weight[k])) return MUFFIN_ERR_ARG;
+      lam.v[k] = h_out_weight[k];
+    }
   if (!d_ws || ((uintptr_t)d_ws & 255)) return MUFFIN_ERR_ARG;
   const Dims d = make_dims(nz, ny, nx);
-  const size_t need = net_layout(nullptr, d, training != 0, nullptr);
+  const size_t need = net_layout(nullptr, d, n_out, training != 0, nullptr);
   if (ws_bytes < need) return MUFFIN_ERR_NOMEM;
-  if (configure_once() != cudaSuccess) return MUFFIN_ERR_CUDA;
+  if (configure_once(n_out) != cudaSuccess) return MUFFIN_ERR_CUDA;
   muffin_net* n = new muffin_net();
   n->training = training != 0;
+  n->K = n_out;
+  n->lam = lam;
   n->d = d;
   n->st = stream;
   n->sms = sm_count();
-  net_layout(n, d, n->training, (char*)d_ws);
-  const int np = param_count();
+  net_layout(n, d, n_out, n->training, (char*)d_ws);
+  const int np = param_count(n_out);
   cudaMemsetAsync(n->theta, 0, np * 4, stream);
   if (n->training) {
     cudaMemsetAsync(n->mom1, 0, np * 4, stream);
@@ -987,7 +1112,7 @@ int muffin_net_create(muffin_net** out, int nz, int ny, int nx, int training, vo
 int muffin_net_set_params(muffin_net* n, const float* d_theta) {
   if (!n) return MUFFIN_ERR_ARG;
   if (!d_theta) return fail(n, MUFFIN_ERR_ARG, "d_theta is NULL");
-  const int np = param_count();
+  const int np = param_count(n->K);
   cudaMemcpyAsync(n->theta, d_theta, np * 4, cudaMemcpyDeviceToDevice, n->st);
   if (n->training) {
     cudaMemsetAsync(n->mom1, 0, np * 4, n->st);
@@ -1000,26 +1125,35 @@ int muffin_net_set_params(muffin_net* n, const float* d_theta) {
 
 int muffin_net_get_params(const muffin_net* n, float* d_theta) {
   if (!n || !d_theta) return MUFFIN_ERR_ARG;
-  cudaMemcpyAsync(d_theta, n->theta, param_count() * 4, cudaMemcpyDeviceToDevice, n->st);
+  cudaMemcpyAsync(d_theta, n->theta, param_count(n->K) * 4, cudaMemcpyDeviceToDevice, n->st);
   return cuda_check(const_cast<muffin_net*>(n), "muffin_net_get_params");
 }
 
-int muffin_net_predict(muffin_net* n, const float* d_dirty, float* d_x) {
+int muffin_net_predict(muffin_net* n, const float* d_dirty, float* d_x, float* d_aux) {
   if (!n) return MUFFIN_ERR_ARG;
   if (!d_dirty || !d_x) return fail(n, MUFFIN_ERR_ARG, "NULL cube pointer");
+  if (n->K > 1 && !d_aux) return fail(n, MUFFIN_ERR_ARG, "NULL d_aux with more than one output map");
   forward_to_a5(n, d_dirty);
-  const int PL = loss_slots(n->d);
-  k_last_fwd<0><<<PL, 256, last_smem, n->st>>>(a5_of(n), n->kw.w6, n->kw.b6, nullptr, n->s, d_x, nullptr, n->d);
+  MNET_SWITCH_K(n->K, last_predict<KK>(n, d_x, d_aux));
   return cuda_check(n, "muffin_net_predict");
 }
 
-int muffin_net_loss_grad(muffin_net* n, const float* d_dirty, const float* d_target, float* d_grad, double* h_loss) {
-  if (!n) return MUFFIN_ERR_ARG;
+static int check_targets(muffin_net* n, const float* d_dirty, const float* d_tx, const void* d_taux) {
   if (!n->training) return fail(n, MUFFIN_ERR_STATE, "not a training context");
-  if (!d_dirty || !d_target || !d_grad) return fail(n, MUFFIN_ERR_ARG, "NULL pointer");
-  loss_and_grad(n, d_dirty, d_target);
-  cudaMemcpyAsync(d_grad, n->grad, param_count() * 4, cudaMemcpyDeviceToDevice, n->st);
-  int r = cuda_check(n, "muffin_net_loss_grad");
+  if (!d_dirty || !d_tx) return fail(n, MUFFIN_ERR_ARG, "NULL pointer");
+  if (n->K > 1 && !d_taux) return fail(n, MUFFIN_ERR_ARG, "NULL d_target_aux with more than one output map");
+  return MUFFIN_OK;
+}
+
+int muffin_net_loss_grad(muffin_net* n, const float* d_dirty, const float* d_tx, const void* d_taux, float* d_grad,
+                         double* h_loss) {
+  if (!n) return MUFFIN_ERR_ARG;
+  int r = check_targets(n, d_dirty, d_tx, d_taux);
+  if (r != MUFFIN_OK) return r;
+  if (!d_grad) return fail(n, MUFFIN_ERR_ARG, "NULL d_grad");
+  loss_and_grad(n, d_dirty, d_tx, (const bf16*)d_taux);
+  cudaMemcpyAsync(d_grad, n->grad, param_count(n->K) * 4, cudaMemcpyDeviceToDevice, n->st);
+  r = cuda_check(n, "muffin_net_loss_grad");
   if (r != MUFFIN_OK) return r;
   if (h_loss) {
     cudaMemcpyAsync(h_loss, n->loss, 8, cudaMemcpyDeviceToHost, n->st);
@@ -1029,24 +1163,25 @@ int muffin_net_loss_grad(muffin_net* n, const float* d_dirty, const float* d_tar
   return MUFFIN_OK;
 }
 
-int muffin_net_train_step(muffin_net* n, const float* d_dirty, const float* d_target, float lr, double* d_loss) {
+int muffin_net_train_step(muffin_net* n, const float* d_dirty, const float* d_tx, const void* d_taux, float lr,
+                          double* d_loss) {
   if (!n) return MUFFIN_ERR_ARG;
-  if (!n->training) return fail(n, MUFFIN_ERR_STATE, "not a training context");
-  if (!d_dirty || !d_target) return fail(n, MUFFIN_ERR_ARG, "NULL pointer");
+  int r = check_targets(n, d_dirty, d_tx, d_taux);
+  if (r != MUFFIN_OK) return r;
   if (!(lr >= 0.f) || !std::isfinite(lr)) return fail(n, MUFFIN_ERR_ARG, "learning rate must be finite and >= 0");
-  loss_and_grad(n, d_dirty, d_target);
+  loss_and_grad(n, d_dirty, d_tx, (const bf16*)d_taux);
   if (d_loss) cudaMemcpyAsync(d_loss, n->loss, 8, cudaMemcpyDeviceToDevice, n->st);
   n->step += 1;
   const double c1 = 1.0 / (1.0 - std::pow(0.9, (double)n->step));
   const double c2 = 1.0 / (1.0 - std::pow(0.999, (double)n->step));
-  const int np = param_count();
+  const int np = param_count(n->K);
   k_adam<<<(np + 255) / 256, 256, 0, n->st>>>(n->theta, n->grad, n->mom1, n->mom2, np, lr, (float)c1, (float)c2);
   unpack_params(n);
   return cuda_check(n, "muffin_net_train_step");
 }
 
 const char* muffin_net_last_error(const muffin_net* n) {
-  if (!n) return "invalid arguments to muffin_net_create (sizes, workspace alignment or size) or CUDA set-up failed";
+  if (!n) return "invalid arguments to muffin_net_create (sizes, output maps, weights, workspace) or CUDA set-up failed";
   return n->err.c_str();
 }
 
@@ -1082,7 +1217,7 @@ static int layer_args(const void* a, const void* b, int nz, int ny, int nx, void
   if (!aligned16(a) || !aligned16(b) || ((uintptr_t)scratch & 255))
     return conv_fail(MUFFIN_ERR_ARG, "maps must be 16-byte aligned, scratch 256-byte aligned");
   if (bytes < muffin_conv3d_scratch_bytes(nz, ny, nx)) return conv_fail(MUFFIN_ERR_NOMEM, "scratch too small");
-  if (configure_once() != cudaSuccess) return conv_fail(MUFFIN_ERR_CUDA, "kernel attributes could not be set");
+  if (configure_once(0) != cudaSuccess) return conv_fail(MUFFIN_ERR_CUDA, "kernel attributes could not be set");
   return MUFFIN_OK;
 }
 

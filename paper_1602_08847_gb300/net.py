@@ -17,14 +17,14 @@ from . import muffin as _m
 _lib = _m.lib
 _P, _I, _S, _F = ctypes.c_void_p, ctypes.c_int, ctypes.c_size_t, ctypes.c_float
 _SIG = {
-    "muffin_net_num_params": (_I, []),
-    "muffin_net_workspace_bytes": (_S, [_I, _I, _I, _I]),
-    "muffin_net_create": (_I, [ctypes.POINTER(_P), _I, _I, _I, _I, _P, _S, _P]),
+    "muffin_net_num_params": (_I, [_I]),
+    "muffin_net_workspace_bytes": (_S, [_I, _I, _I, _I, _I]),
+    "muffin_net_create": (_I, [ctypes.POINTER(_P), _I, _I, _I, _I, ctypes.POINTER(_F), _I, _P, _S, _P]),
     "muffin_net_set_params": (_I, [_P, _P]),
     "muffin_net_get_params": (_I, [_P, _P]),
-    "muffin_net_predict": (_I, [_P, _P, _P]),
-    "muffin_net_loss_grad": (_I, [_P, _P, _P, _P, ctypes.POINTER(ctypes.c_double)]),
-    "muffin_net_train_step": (_I, [_P, _P, _P, _F, _P]),
+    "muffin_net_predict": (_I, [_P, _P, _P, _P]),
+    "muffin_net_loss_grad": (_I, [_P, _P, _P, _P, _P, ctypes.POINTER(ctypes.c_double)]),
+    "muffin_net_train_step": (_I, [_P, _P, _P, _P, _F, _P]),
     "muffin_net_last_error": (ctypes.c_char_p, [_P]),
     "muffin_net_destroy": (None, [_P]),
     "muffin_conv3d_scratch_bytes": (_S, [_I, _I, _I]),
@@ -38,8 +38,18 @@ for _name, (_res, _args) in _SIG.items():
     _fn.restype = _res
     _fn.argtypes = _args
 
-N_PARAMS = int(_lib.muffin_net_num_params())
 FEATURES = 32
+
+
+def n_params(n_out: int = 1) -> int:
+    """Packed parameter count of the network with n_out output maps."""
+    n = int(_lib.muffin_net_num_params(int(n_out)))
+    if n == 0:
+        raise ValueError(f"n_out must be in [1, 8], got {n_out}")
+    return n
+
+
+N_PARAMS = n_params(1)
 
 
 def _ptr(t):
@@ -59,19 +69,31 @@ def _map(t: torch.Tensor, shape, name: str) -> torch.Tensor:
 
 
 class WarmStartNet:
-    """The network on nz x ny x nx cubes (a libmuffin network context)."""
+    """The network on nz x ny x nx cubes (a libmuffin network context).
 
-    def __init__(self, shape, training: bool = False, theta: torch.Tensor | None = None):
+    n_out output maps: map 0 predicts the cube, maps 1 .. n_out-1 further
+    fields of the state (the planes of the wavelet dual U when n_out = J + 2);
+    out_weight gives the n_out loss weights (default all 1)."""
+
+    def __init__(self, shape, training: bool = False, theta: torch.Tensor | None = None, n_out: int = 1,
+                 out_weight=None):
         self.shape = tuple(int(s) for s in shape)
         nz, ny, nx = self.shape
         self.training = bool(training)
-        nbytes = int(_lib.muffin_net_workspace_bytes(nz, ny, nx, int(self.training)))
+        self.n_out = int(n_out)
+        self.n_params = n_params(self.n_out)
+        nbytes = int(_lib.muffin_net_workspace_bytes(nz, ny, nx, self.n_out, int(self.training)))
         if nbytes == 0:
             raise ValueError(f"invalid cube shape {self.shape}")
+        lam = None
+        if out_weight is not None:
+            if len(out_weight) != self.n_out:
+                raise ValueError("out_weight needs one value per output map")
+            lam = (_F * self.n_out)(*[float(v) for v in out_weight])
         self._ws = torch.empty(nbytes, dtype=torch.uint8, device="cuda")
         self._net = _P()
-        r = _lib.muffin_net_create(ctypes.byref(self._net), nz, ny, nx, int(self.training), self._ws.data_ptr(),
-                                   nbytes, torch.cuda.current_stream().cuda_stream)
+        r = _lib.muffin_net_create(ctypes.byref(self._net), nz, ny, nx, self.n_out, lam, int(self.training),
+                                   self._ws.data_ptr(), nbytes, torch.cuda.current_stream().cuda_stream)
         if r != 0:
             raise _m.MuffinError(r, _lib.muffin_net_last_error(None).decode())
         if theta is not None:
@@ -89,41 +111,56 @@ class WarmStartNet:
 
     def set_params(self, theta: torch.Tensor):
         theta = _dev_f32(theta.reshape(-1), "theta")
-        if theta.numel() != N_PARAMS:
-            raise ValueError(f"theta has {theta.numel()} values, expected {N_PARAMS}")
+        if theta.numel() != self.n_params:
+            raise ValueError(f"theta has {theta.numel()} values, expected {self.n_params}")
         self._check(_lib.muffin_net_set_params(self._net, theta.data_ptr()))
 
     def get_params(self) -> torch.Tensor:
-        out = torch.empty(N_PARAMS, dtype=torch.float32, device="cuda")
+        out = torch.empty(self.n_params, dtype=torch.float32, device="cuda")
         self._check(_lib.muffin_net_get_params(self._net, out.data_ptr()))
         return out
 
-    def predict(self, dirty: torch.Tensor, out: torch.Tensor | None = None) -> torch.Tensor:
-        self._cube(dirty, "dirty")
-        if out is None:
-            out = torch.empty_like(dirty)
-        self._cube(out, "out")
-        self._check(_lib.muffin_net_predict(self._net, dirty.data_ptr(), out.data_ptr()))
-        return out
+    def _aux_shape(self):
+        nz, ny, nx = self.shape
+        return (nz, self.n_out - 1, ny, nx)
 
-    def loss_grad(self, dirty: torch.Tensor, target: torch.Tensor) -> tuple[float, torch.Tensor]:
+    def _aux_target(self, t):
+        if self.n_out == 1:
+            return None
+        if t is None or not (t.is_cuda and t.dtype == torch.bfloat16 and t.is_contiguous()) \
+                or tuple(t.shape) != self._aux_shape():
+            raise ValueError(f"target_aux must be a contiguous bfloat16 CUDA tensor of shape {self._aux_shape()}")
+        return t
+
+    def predict(self, dirty: torch.Tensor):
+        """(cube [nz][ny][nx], fields [nz][n_out-1][ny][nx] or None)."""
         self._cube(dirty, "dirty")
-        self._cube(target, "target")
-        g = torch.empty(N_PARAMS, dtype=torch.float32, device="cuda")
+        x = torch.empty_like(dirty)
+        aux = torch.empty(self._aux_shape(), dtype=torch.float32, device="cuda") if self.n_out > 1 else None
+        self._check(_lib.muffin_net_predict(self._net, dirty.data_ptr(), x.data_ptr(), _ptr(aux)))
+        return x, aux
+
+    def loss_grad(self, dirty: torch.Tensor, target_x: torch.Tensor,
+                  target_aux: torch.Tensor | None = None) -> tuple[float, torch.Tensor]:
+        self._cube(dirty, "dirty")
+        self._cube(target_x, "target_x")
+        ta = self._aux_target(target_aux)
+        g = torch.empty(self.n_params, dtype=torch.float32, device="cuda")
         loss = ctypes.c_double()
-        self._check(_lib.muffin_net_loss_grad(self._net, dirty.data_ptr(), target.data_ptr(), g.data_ptr(),
-                                              ctypes.byref(loss)))
+        self._check(_lib.muffin_net_loss_grad(self._net, dirty.data_ptr(), target_x.data_ptr(), _ptr(ta),
+                                              g.data_ptr(), ctypes.byref(loss)))
         return loss.value, g
 
-    def train_step(self, dirty: torch.Tensor, target: torch.Tensor, lr: float,
+    def train_step(self, dirty: torch.Tensor, target_x: torch.Tensor, target_aux: torch.Tensor | None, lr: float,
                    loss_out: torch.Tensor | None = None):
         """One Adam step; loss_out (a float64 CUDA scalar) receives the loss."""
         self._cube(dirty, "dirty")
-        self._cube(target, "target")
+        self._cube(target_x, "target_x")
+        ta = self._aux_target(target_aux)
         if loss_out is not None and not (loss_out.is_cuda and loss_out.dtype == torch.float64):
             raise ValueError("loss_out must be a float64 CUDA tensor")
-        self._check(_lib.muffin_net_train_step(self._net, dirty.data_ptr(), target.data_ptr(), float(lr),
-                                               _ptr(loss_out)))
+        self._check(_lib.muffin_net_train_step(self._net, dirty.data_ptr(), target_x.data_ptr(), _ptr(ta),
+                                               float(lr), _ptr(loss_out)))
 
     def close(self):
         if getattr(self, "_net", None) is not None and self._net.value:
@@ -193,17 +230,29 @@ def conv3d_backward_weights(a: torch.Tensor, dz: torch.Tensor) -> tuple[torch.Te
 
 # ---------------------------------------------------------------- warm start of Algorithm 1
 
-def warm_start(problem, net: WarmStartNet, dirty: torch.Tensor) -> dict:
-    """Start ``problem`` (a muffin.Muffin at pass 0) from the network's cube.
+def warm_start(problem, net: WarmStartNet, net_input: torch.Tensor, keep_state: bool = False) -> dict:
+    """Move ``problem`` (a muffin.Muffin) to the network's state.
 
-    The plain method's start X = 0 stays the fallback and the judge: the
-    prediction is kept only if the objective of Eqs. 5-6 is lower there than
-    at X = 0.  Returns what was decided and both objectives."""
+    The network maps ``net_input`` (the dirty cube, or the cube after a few
+    passes) to the cube X and, when it has J + 2 output maps, the wavelet
+    dual U.  V is kept when ``keep_state`` (else 0), and so is U when the
+    network does not give it.  The method's own state stays the fallback and
+    the judge: the prediction is kept only if the objective of Eqs. 5-6 is
+    lower at the predicted X than at the current one.  Returns what was
+    decided and both objectives."""
     f0, _ = problem.objective()
-    x = net.predict(dirty)
-    problem.set_cube(x)
+    x0, u0, v0, it = problem.get_state()
+    if not keep_state:
+        x0, u0, v0, it = torch.zeros_like(x0), torch.zeros_like(u0), torch.zeros_like(v0), 0
+    x, aux = net.predict(net_input)
+    u = u0
+    if aux is not None:
+        if aux.shape[1] != problem.nscales + 1:
+            raise ValueError(f"network gives {aux.shape[1]} fields, the problem has {problem.nscales + 1} planes of U")
+        u = aux
+    problem.set_state(x, u, v0, it)
     f1, _ = problem.objective()
     used = f1 < f0
     if not used:
-        problem.set_cube(torch.zeros_like(x))
-    return {"used": bool(used), "f_zero": f0, "f_net": f1}
+        problem.set_state(x0, u0, v0, it)
+    return {"used": bool(used), "f_start": f0, "f_net": f1}

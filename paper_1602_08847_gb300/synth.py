@@ -178,17 +178,26 @@ def bf16_round(a) -> np.ndarray:
     return u.astype(np.uint32).view(np.float32)
 
 
-def net_init(seed: int, bf16: bool = True) -> np.ndarray:
-    """Seeded initial parameters of the network, packed layer by layer as
-    weights [co][ci][3][3][3] then biases [co]: He-normal weights
-    (std sqrt(2 / (27 ci))), zero biases; the last layer is scaled down by 10 so
-    the first predictions are small."""
+def net_init(seed: int, n_out: int = 1, bf16: bool = True) -> np.ndarray:
+    """Seeded initial parameters of the network with n_out output maps, packed
+    layer by layer as weights [co][ci][3][3][3] then biases [co]: He-normal
+    weights (std sqrt(2 / (27 ci))), zero biases; the last layer is scaled down
+    by 10 so the first predictions are small."""
     rng = np.random.Generator(np.random.PCG64(seed))
     parts = []
-    for k, (ci, co) in enumerate(NET_LAYERS):
+    layers = NET_LAYERS[:-1] + ((NET_LAYERS[-1][0], n_out),)
+    for k, (ci, co) in enumerate(layers):
         w = rng.standard_normal(co * ci * 27) * np.sqrt(2.0 / (27 * ci))
-        if k == len(NET_LAYERS) - 1:
+        if k == len(layers) - 1:
             w *= 0.1
         parts += [w, np.zeros(co)]
     theta = np.concatenate(parts).astype(np.float32)
     return bf16_round(theta) if bf16 else theta
+
+
+def cube_arrays(args) -> tuple:
+    """(seed, dirty, psf) of make_cube(cfg, seed) for args = (cfg, seed); a
+    top-level function so that worker processes can build cubes in parallel."""
+    cfg, seed = args
+    c = make_cube(cfg, seed=seed)
+    return seed, c.dirty, c.psf

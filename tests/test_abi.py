@@ -75,22 +75,29 @@ def test_init_rejects_bad_arguments_before_any_cuda_call():
 
 def test_net_sizes_and_create_argument_checks(so):
     so.muffin_net_workspace_bytes.restype = ctypes.c_size_t
-    so.muffin_net_workspace_bytes.argtypes = [ctypes.c_int] * 4
+    so.muffin_net_workspace_bytes.argtypes = [ctypes.c_int] * 5
     so.muffin_conv3d_scratch_bytes.restype = ctypes.c_size_t
     so.muffin_conv3d_scratch_bytes.argtypes = [ctypes.c_int] * 3
     so.muffin_net_create.argtypes = [ctypes.POINTER(ctypes.c_void_p), ctypes.c_int, ctypes.c_int, ctypes.c_int,
-                                     ctypes.c_int, ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p]
-    assert so.muffin_net_num_params() == 112481
-    infer = so.muffin_net_workspace_bytes(64, 256, 256, 0)
-    train = so.muffin_net_workspace_bytes(64, 256, 256, 1)
+                                     ctypes.c_int, ctypes.POINTER(ctypes.c_float), ctypes.c_int, ctypes.c_void_p,
+                                     ctypes.c_size_t, ctypes.c_void_p]
+    so.muffin_net_num_params.argtypes = [ctypes.c_int]
+    assert so.muffin_net_num_params(1) == 112481
+    assert so.muffin_net_num_params(6) == 112481 + 5 * 865
+    assert so.muffin_net_num_params(0) == 0 and so.muffin_net_num_params(9) == 0
+    infer = so.muffin_net_workspace_bytes(64, 256, 256, 1, 0)
+    train = so.muffin_net_workspace_bytes(64, 256, 256, 6, 1)
     V = 64 * 256 * 256
-    assert infer >= V * 2 + 2 * V * 64          # input map + two feature maps
-    assert train >= V * 2 + 7 * V * 64 + V * 4  # five kept maps, two gradient maps, loss gradient
-    assert so.muffin_net_workspace_bytes(0, 4, 4, 0) == 0
-    assert so.muffin_net_workspace_bytes(1 << 20, 1 << 10, 1 << 10, 0) == 0
+    assert infer >= V * 2 + 2 * V * 64               # input map + two feature maps
+    assert train >= V * 2 + 7 * V * 64 + 6 * V * 4   # five kept maps, two gradient maps, loss gradients
+    assert so.muffin_net_workspace_bytes(0, 4, 4, 1, 0) == 0
+    assert so.muffin_net_workspace_bytes(4, 4, 4, 9, 0) == 0
+    assert so.muffin_net_workspace_bytes(1 << 20, 1 << 10, 1 << 10, 1, 0) == 0
     assert so.muffin_conv3d_scratch_bytes(3, 5, 7) > 27648 * 2
     net = ctypes.c_void_p()
-    assert so.muffin_net_create(ctypes.byref(net), 0, 8, 8, 0, None, 0, None) == -1
-    assert so.muffin_net_create(ctypes.byref(net), 4, 8, 8, 0, None, 1 << 20, None) == -1
-    assert so.muffin_net_create(ctypes.byref(net), 4, 8, 8, 0, ctypes.c_void_p(256), 16, None) == -3
+    assert so.muffin_net_create(ctypes.byref(net), 0, 8, 8, 1, None, 0, None, 0, None) == -1
+    assert so.muffin_net_create(ctypes.byref(net), 4, 8, 8, 1, None, 0, None, 1 << 20, None) == -1
+    neg = (ctypes.c_float * 2)(1.0, -1.0)
+    assert so.muffin_net_create(ctypes.byref(net), 4, 8, 8, 2, neg, 0, ctypes.c_void_p(256), 1 << 30, None) == -1
+    assert so.muffin_net_create(ctypes.byref(net), 4, 8, 8, 1, None, 0, ctypes.c_void_p(256), 16, None) == -3
     assert not net.value

@@ -102,6 +102,56 @@ def rel(a, b):
     return float(np.linalg.norm(a - b) / np.linalg.norm(b))
 
 
+def bf16(a):
+    return synth.bf16_round(a).astype(np.float64)
+
+
+def gradient_at_bf16_points(theta, y, t, arch, t_aux=None, lam=None):
+    """The oracle's gradient with the feature maps and the back-propagated
+    map gradients rounded to bfloat16 where the kernels store them (weights
+    rounded too; sums exact).  Its distance to the exact gradient measures how
+    far bfloat16 storage alone moves the result on this input."""
+    layers = wn.unpack(theta, arch)
+    s = wn.input_scale(y)
+    a = bf16(np.asarray(y)[None] / s)
+    acts = [a]
+    for k, ((w, b), (_, _, relu)) in enumerate(zip(layers, arch)):
+        z = wn.conv3d(a, bf16(w), b)
+        a = bf16(np.maximum(z, 0.0)) if relu else z
+        acts.append(a)
+    z = acts[-1]
+    K = z.shape[0]
+    target = np.empty_like(z)
+    target[0] = t / s
+    if K > 1:
+        target[1:] = t_aux
+    lam = np.ones(K) if lam is None else np.asarray(lam)
+    dz = (2.0 / z[0].size) * lam[:, None, None, None] * (z - target)
+    grads = [None] * len(layers)
+    for k in range(len(layers) - 1, -1, -1):
+        da, dw, db = wn.conv3d_backward(acts[k], bf16(layers[k][0]), dz)
+        grads[k] = (dw, db)
+        if k > 0:
+            dz = bf16(da * (acts[k] > 0.0))
+    return wn.pack(grads)
+
+
+def check_gradient(g, theta, y, t, arch, t_aux=None, lam=None):
+    """Per layer: the GPU gradient lies within twice the bfloat16-storage
+    envelope of the exact gradient, plus 1 %."""
+    _, g_ref = wn.gradient(theta, y, t, arch, t_aux, lam)
+    g_bf = gradient_at_bf16_points(theta, y, t, arch, t_aux, lam)
+    off = 0
+    for ci, co, _ in arch:
+        nw = co * ci * 27
+        for part in (slice(off, off + nw), slice(off + nw, off + nw + co)):
+            envelope = rel(g_bf[part], g_ref[part])
+            assert rel(g[part], g_ref[part]) <= 2 * envelope + 1e-2, (ci, co, rel(g[part], g_ref[part]), envelope)
+            cos = np.dot(g[part], g_ref[part]) / np.linalg.norm(g[part]) / np.linalg.norm(g_ref[part])
+            assert cos > 0.995
+        off += nw + co
+
+
 @pytest.mark.parametrize("shape", [(4, 12, 20), (3, 16, 16)])
 def test_network_prediction(netmod, shape):
     theta = synth.net_init(7).astype(np.float64)
@@ -109,7 +159,9 @@ def test_network_prediction(netmod, shape):
     ref, _, _ = wn.forward(theta, y)
     ref = np.maximum(ref, 0.0)
     n = netmod.WarmStartNet(shape, theta=torch.from_numpy(theta.astype(np.float32)).cuda())
-    got = n.predict(torch.from_numpy(y.astype(np.float32)).cuda()).cpu().numpy().astype(np.float64)
+    got, aux = n.predict(torch.from_numpy(y.astype(np.float32)).cuda())
+    assert aux is None
+    got = got.cpu().numpy().astype(np.float64)
     # five bfloat16 feature maps, each rounded to 2^-9 relative: well inside 2 %
     assert rel(got, ref) < 2e-2, rel(got, ref)
     assert np.all(got >= 0)
@@ -125,15 +177,37 @@ def test_network_loss_and_gradient(netmod):
     loss, g = n.loss_grad(torch.from_numpy(y.astype(np.float32)).cuda(), torch.from_numpy(t.astype(np.float32)).cuda())
     g = g.cpu().numpy().astype(np.float64)
     assert abs(loss - loss_ref) <= 1e-2 * loss_ref
-    off = 0
-    for ci, co, _ in wn.ARCH:
-        nw = co * ci * 27
-        for part in (slice(off, off + nw), slice(off + nw, off + nw + co)):
-            # bfloat16 feature maps and bfloat16 back-propagated gradients
-            assert rel(g[part], g_ref[part]) < 3e-2, (ci, co, rel(g[part], g_ref[part]))
-            cos = np.dot(g[part], g_ref[part]) / np.linalg.norm(g[part]) / np.linalg.norm(g_ref[part])
-            assert cos > 0.999
-        off += nw + co
+    check_gradient(g, theta, y, t, wn.ARCH)
+
+
+def test_network_with_dual_outputs(netmod):
+    """Six output maps (the cube and five planes of U): prediction, loss and
+    gradient with per-map weights and bfloat16 field targets."""
+    shape, K = (3, 10, 18), 6
+    arch = wn.arch(K)
+    rng = np.random.Generator(np.random.PCG64(21))
+    theta = synth.bf16_round(rng.normal(0.0, 0.05, wn.n_params(arch)).astype(np.float32)).astype(np.float64)
+    theta[:wn.n_params(wn.ARCH) - 865] = synth.net_init(11)[:wn.n_params(wn.ARCH) - 865]
+    y, t = net_inputs(shape, 15)
+    t_aux = bf((K - 1,) + shape, 16)
+    lam = np.array([50.0, 1.0, 2.0, 0.5, 1.0, 3.0])
+    # prediction: cube and clamped fields
+    ref_x, acts, s = wn.forward(theta, y, arch)
+    n = netmod.WarmStartNet(shape, theta=torch.from_numpy(theta.astype(np.float32)).cuda(), n_out=K)
+    x, aux = n.predict(torch.from_numpy(y.astype(np.float32)).cuda())
+    ref_aux = np.clip(acts[-1][1:], -1, 1).transpose(1, 0, 2, 3)       # [nz][K-1][ny][nx]
+    assert rel(x.cpu().numpy().astype(np.float64), np.maximum(ref_x, 0)) < 2e-2
+    assert rel(aux.cpu().numpy().astype(np.float64), ref_aux) < 2e-2
+    # loss and gradient
+    loss_ref, g_ref = wn.gradient(theta, y, t, arch, t_aux, lam)
+    n = netmod.WarmStartNet(shape, training=True, theta=torch.from_numpy(theta.astype(np.float32)).cuda(), n_out=K,
+                            out_weight=lam)
+    ta = torch.from_numpy(np.ascontiguousarray(t_aux.transpose(1, 0, 2, 3)).astype(np.float32)).cuda()
+    loss, g = n.loss_grad(torch.from_numpy(y.astype(np.float32)).cuda(), torch.from_numpy(t.astype(np.float32)).cuda(),
+                          ta.to(torch.bfloat16))
+    g = g.cpu().numpy().astype(np.float64)
+    assert abs(loss - loss_ref) <= 1e-2 * loss_ref
+    check_gradient(g, theta, y, t, arch, t_aux, lam)
 
 
 def test_first_adam_step_moves_by_lr_times_sign(netmod):
@@ -143,7 +217,7 @@ def test_first_adam_step_moves_by_lr_times_sign(netmod):
     dev = lambda a: torch.from_numpy(np.ascontiguousarray(a, dtype=np.float32)).cuda()  # noqa: E731
     n = netmod.WarmStartNet(shape, training=True, theta=dev(theta))
     _, g = n.loss_grad(dev(y), dev(t))
-    n.train_step(dev(y), dev(t), 1e-3)
+    n.train_step(dev(y), dev(t), None, 1e-3)
     step = (n.get_params().cpu().numpy() - theta).astype(np.float64)
     g = g.cpu().numpy().astype(np.float64)
     big = np.abs(g) > 1e-5
@@ -159,7 +233,7 @@ def test_training_lowers_the_loss(netmod):
     yd, td = dev(y), dev(t)
     first, _ = n.loss_grad(yd, td)
     for _ in range(60):
-        n.train_step(yd, td, 2e-3)
+        n.train_step(yd, td, None, 2e-3)
     last, _ = n.loss_grad(yd, td)
     assert last < 0.5 * first, (first, last)
 
@@ -167,8 +241,13 @@ def test_training_lowers_the_loss(netmod):
 def test_network_argument_errors(netmod):
     with pytest.raises(ValueError):
         netmod.WarmStartNet((0, 8, 8))
+    with pytest.raises(ValueError):
+        netmod.WarmStartNet((2, 8, 8), n_out=9)
     n = netmod.WarmStartNet((2, 8, 8))
     with pytest.raises(ValueError):
         n.predict(torch.zeros((2, 8, 9), device="cuda"))
+    m = netmod.WarmStartNet((2, 8, 8), training=True, n_out=3)
+    with pytest.raises(ValueError):                      # the fields' target is missing
+        m.loss_grad(torch.zeros((2, 8, 8), device="cuda"), torch.zeros((2, 8, 8), device="cuda"))
     with pytest.raises(Exception):
         n.loss_grad(torch.zeros((2, 8, 8), device="cuda"), torch.zeros((2, 8, 8), device="cuda"))

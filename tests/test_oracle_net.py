@@ -71,20 +71,40 @@ def _fd_check(arch, shape, seed, n_sample=None, h=1e-5):
     theta = rng.normal(0.0, 0.4, wn.n_params(arch))
     y = rng.uniform(-0.5, 1.0, shape)
     t = rng.uniform(0.0, 1.0, shape)
-    _, g = wn.gradient(theta, y, t, arch)
+    K = arch[-1][1]
+    t_aux = rng.uniform(-1.0, 1.0, (K - 1,) + shape) if K > 1 else None
+    lam = rng.uniform(0.5, 3.0, K)
+    _, g = wn.gradient(theta, y, t, arch, t_aux, lam)
     idx = np.arange(theta.size) if n_sample is None else rng.choice(theta.size, n_sample, replace=False)
     fd = np.empty(idx.size)
     for n, i in enumerate(idx):
         tp, tm = theta.copy(), theta.copy()
         tp[i] += h
         tm[i] -= h
-        fd[n] = (wn.loss(tp, y, t, arch) - wn.loss(tm, y, t, arch)) / (2 * h)
+        fd[n] = (wn.loss(tp, y, t, arch, t_aux, lam) - wn.loss(tm, y, t, arch, t_aux, lam)) / (2 * h)
     return g[idx], fd
 
 
 def test_gradient_matches_central_differences_small_net():
     g, fd = _fd_check(SMALL, (3, 4, 4), 9)
     assert np.linalg.norm(g - fd) <= 1e-7 * np.linalg.norm(fd)
+
+
+def test_gradient_matches_central_differences_several_outputs():
+    """Three output maps (the cube and two further fields), weighted loss."""
+    small3 = SMALL[:-1] + ((2, 3, False),)
+    g, fd = _fd_check(small3, (3, 4, 4), 19)
+    assert np.linalg.norm(g - fd) <= 1e-7 * np.linalg.norm(fd)
+
+
+def test_loss_weights_and_targets_enter_as_defined():
+    """lam = (0, 1) and a zero network: loss = mean of the aux target squared."""
+    K = 2
+    theta = np.zeros(wn.n_params(wn.arch(K)))
+    y = rnd((2, 3, 4), 20)
+    t_aux = rnd((1, 2, 3, 4), 21)
+    val = wn.loss(theta, y, rnd((2, 3, 4), 22), wn.arch(K), t_aux, (0.0, 1.0))
+    assert np.isclose(val, np.mean(t_aux[0] ** 2), rtol=1e-14)
 
 
 def test_gradient_matches_central_differences_full_net():
@@ -147,11 +167,11 @@ def test_planted_mistakes_are_caught(plant, monkeypatch):
     if plant == "no_relu_mask":
         orig = wn.gradient
 
-        def wrong(theta, y, t, arch=wn.ARCH):
+        def wrong(theta, y, t, arch=wn.ARCH, t_aux=None, lam=None):
             layers = wn.unpack(theta, arch)
             _, acts, s = wn.forward(theta, y, arch)
             r = acts[-1][0] - t / s
-            dz = (2.0 / r.size) * r[None]
+            dz = (2.0 / r.size) * lam[0] * r[None]
             grads = [None] * len(layers)
             for k in range(len(layers) - 1, -1, -1):
                 da, dw, db = wn.conv3d_backward(acts[k], layers[k][0], dz)
