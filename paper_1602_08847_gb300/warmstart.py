@@ -195,6 +195,25 @@ def summarise(results: list[dict]) -> dict:
     return s
 
 
+WEIGHTS = os.path.join(os.path.dirname(os.path.abspath(__file__)), "weights", "warmstart_256x256x64.npy")
+
+
+def load_committed(path: str = WEIGHTS):
+    """(WarmStartNet for 64 x 256 x 256 cubes, training record) from the
+    weights shipped with the package, or (None, {}) when there are none."""
+    if not os.path.exists(path):
+        return None, {}
+    meta = {}
+    rec = os.path.splitext(path)[0] + ".json"
+    if os.path.exists(rec):
+        with open(rec) as f:
+            meta = json.load(f)
+    theta = torch.from_numpy(np.load(path).astype(np.float32)).cuda()
+    n_out = {n_params(k): k for k in range(1, 9)}[theta.numel()]
+    shape = tuple(meta.get("shape", (64, 256, 256)))
+    return WarmStartNet(shape, theta=theta, n_out=n_out), meta
+
+
 def _seeds(spec: str):
     a, b = spec.split(":")
     return range(int(a), int(b))
