@@ -30,7 +30,7 @@ def dense_operators(p: mo.Problem):
     L, n, _ = p.shape
     shape = (L, n, n)
     H = operator_matrix(lambda x: mo.apply_H(x, p.hhat), shape)
-    Ws = operator_matrix(lambda x: mo.iuwt_analysis(x, p.J, p.gen), shape)
+    Ws = operator_matrix(lambda x: mo.ws_analysis(p, x), shape)
     Wl = np.kron(mo.dct_matrix(L), np.eye(n * n))
     return H, Ws, Wl
 
@@ -86,9 +86,9 @@ def kkt_residuals(p: mo.Problem, s: mo.State, tol_zero: float = 1e-9) -> dict:
     g >= 0 where X = 0.  Returns the largest violation of each.
     """
     X, U, V = s.X, s.U, s.V
-    g = mo.gradient(X, p.y, p.hhat, p.w) + p.mu_s * mo.iuwt_adjoint(U, p.J, p.gen) \
+    g = mo.gradient(X, p.y, p.hhat, p.w) + p.mu_s * mo.ws_adjoint(p, U) \
         + p.mu_l * mo.spectral_adjoint(V)
-    ws = mo.iuwt_analysis(X, p.J, p.gen)
+    ws = mo.ws_analysis(p, X)
     wl = mo.spectral_analysis(X)
     scale = max(1.0, float(np.abs(g).max()))
     out = {

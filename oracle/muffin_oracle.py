@@ -35,6 +35,7 @@ Readings of the paper taken here (each also listed in the design notes):
 """
 from __future__ import annotations
 
+import functools
 from dataclasses import dataclass
 
 import numpy as np
@@ -181,6 +182,121 @@ def iuwt_norm2_closed_form(n: int, J: int, gen: int = 1) -> float:
 
 
 # --------------------------------------------------------------------------
+# W_s as a union of eight orthonormal Daubechies wavelet bases (Sec. 4)
+# --------------------------------------------------------------------------
+# The comparison dictionary of Sec. 4 (the one of MUFFIN v1): W_s x is the
+# concatenation of the 2D periodic discrete wavelet transforms of x in the
+# Daubechies bases with 1 .. 8 vanishing moments, J levels each, scaled by
+# 1/sqrt(8) so that W_s^T W_s = I (a tight frame; the scale is a reading).
+# Daubechies filters are built from their definition: the lowpass filter
+# H(z) = sqrt(2) ((1 + z^-1)/2)^p Q(z) with |Q(e^iw)|^2 = P(sin^2(w/2)),
+# P(y) = sum_{k<p} C(p-1+k, k) y^k, and Q keeping the zeros inside the unit
+# circle (the minimum-phase choice), normalised to Q(1) = 1.
+
+DB_BASES = 8
+
+
+def daubechies_lowpass(p: int) -> np.ndarray:
+    """h[0 .. 2p-1] of the Daubechies filter with p vanishing moments, H(z) = sum_t h[t] z^-t."""
+    return _daubechies_lowpass(p).copy()
+
+
+@functools.lru_cache(maxsize=None)
+def _daubechies_lowpass(p: int) -> np.ndarray:
+    from math import comb
+    q = np.array([1.0 + 0j])
+    if p > 1:
+        P = [comb(p - 1 + k, k) for k in range(p)]          # ascending powers of y
+        for yk in np.roots(P[::-1]):
+            a = 1.0 - 2.0 * yk                               # y = (2 - z - 1/z)/4  <=>  z^2 - 2a z + 1 = 0
+            r = np.sqrt(a * a - 1.0 + 0j)
+            zk = a + r if abs(a + r) < 1.0 else a - r
+            q = np.convolve(q, np.array([1.0, -zk])) / (1.0 - zk)
+    binom = np.array([comb(p, t) for t in range(p + 1)], dtype=np.float64) / 2.0 ** p
+    return np.sqrt(2.0) * np.real(np.convolve(binom, q))
+
+
+def daubechies_highpass(h: np.ndarray) -> np.ndarray:
+    """g[t] = (-1)^t h[2p-1-t]: the orthogonal mirror filter."""
+    t = np.arange(h.size)
+    return (-1.0) ** t * h[::-1]
+
+
+def dwt_step(x: np.ndarray, h: np.ndarray, axis: int) -> np.ndarray:
+    """One periodic analysis step along an axis of even length M:
+    lo[k] = sum_t h[t] x[(2k+t) mod M], hi[k] = sum_t g[t] x[(2k+t) mod M],
+    returned as [lo | hi] along that axis."""
+    g = daubechies_highpass(h)
+    M = x.shape[axis]
+    k = np.arange(M // 2)
+    lo = sum(h[t] * np.take(x, (2 * k + t) % M, axis=axis) for t in range(h.size))
+    hi = sum(g[t] * np.take(x, (2 * k + t) % M, axis=axis) for t in range(h.size))
+    return np.concatenate([lo, hi], axis=axis)
+
+
+def dwt_step_adjoint(c: np.ndarray, h: np.ndarray, axis: int) -> np.ndarray:
+    """Adjoint of dwt_step: x[(2k+t) mod M] += h[t] lo[k] + g[t] hi[k]."""
+    g = daubechies_highpass(h)
+    M = c.shape[axis]
+    lo = np.take(c, np.arange(M // 2), axis=axis)
+    hi = np.take(c, np.arange(M // 2, M), axis=axis)
+    x = np.zeros_like(c)
+    xm = np.moveaxis(x, axis, 0)
+    lom, him = np.moveaxis(lo, axis, 0), np.moveaxis(hi, axis, 0)
+    k = np.arange(M // 2)
+    for t in range(h.size):
+        xm[(2 * k + t) % M] += h[t] * lom + g[t] * him     # the M/2 targets are distinct for a fixed t
+    return x
+
+
+@functools.lru_cache(maxsize=None)
+def _step_matrices(hkey: bytes, M: int):
+    """(A, B): the matrices of dwt_step and dwt_step_adjoint on length-M vectors,
+    column i the image of unit vector i (so the iteration runs as matmuls)."""
+    h = np.frombuffer(hkey, dtype=np.float64)
+    eye = np.eye(M)
+    return dwt_step(eye, h, axis=0), dwt_step_adjoint(eye, h, axis=0)
+
+
+def dwt2(x: np.ndarray, h: np.ndarray, J: int) -> np.ndarray:
+    """J-level periodic 2D DWT of [..][N][N] images in the Mallat layout: level j
+    transforms the top-left (N/2^j)^2 square (rows, then columns) by dwt_step."""
+    c = np.array(x, dtype=np.float64, copy=True)
+    M = c.shape[-1]
+    for _ in range(J):
+        A, _ = _step_matrices(np.asarray(h, dtype=np.float64).tobytes(), M)
+        sq = c[..., :M, :M] @ A.T                     # dwt_step along rows
+        c[..., :M, :M] = np.einsum("ij,...jk->...ik", A, sq)   # dwt_step along columns
+        M //= 2
+    return c
+
+
+def dwt2_adjoint(c: np.ndarray, h: np.ndarray, J: int) -> np.ndarray:
+    """Adjoint of dwt2: the levels in reverse order, each by dwt_step_adjoint along
+    columns, then along rows."""
+    x = np.array(c, dtype=np.float64, copy=True)
+    N = x.shape[-1]
+    for j in reversed(range(J)):
+        M = N >> j
+        _, B = _step_matrices(np.asarray(h, dtype=np.float64).tobytes(), M)
+        sq = np.einsum("ij,...jk->...ik", B, x[..., :M, :M])
+        x[..., :M, :M] = sq @ B.T
+    return x
+
+
+def union_analysis(x: np.ndarray, J: int) -> np.ndarray:
+    """W_s x for the union of bases: [L][N][N] -> [L][8][N][N]."""
+    s = 1.0 / np.sqrt(DB_BASES)
+    return np.stack([s * dwt2(x, daubechies_lowpass(p), J) for p in range(1, DB_BASES + 1)], axis=1)
+
+
+def union_adjoint(u: np.ndarray, J: int) -> np.ndarray:
+    """W_s^T u for the union of bases: [L][8][N][N] -> [L][N][N]."""
+    s = 1.0 / np.sqrt(DB_BASES)
+    return sum(s * dwt2_adjoint(u[:, p - 1], daubechies_lowpass(p), J) for p in range(1, DB_BASES + 1))
+
+
+# --------------------------------------------------------------------------
 # W_lambda: orthonormal cosine transform along the channel axis
 # --------------------------------------------------------------------------
 
@@ -238,6 +354,7 @@ class Problem:
     sigma: float = 1.0
     rho: float = 1.0
     w: np.ndarray = None     # [L] channel weights 1/sigma_l^2
+    dictionary: str = "iuwt"  # W_s: "iuwt" (Sec. 3) or "union" (eight Daubechies bases, Sec. 4)
 
     def __post_init__(self):
         self.y = np.asarray(self.y, dtype=np.float64)
@@ -261,9 +378,23 @@ class State:
         return State(self.X.copy(), self.U.copy(), self.V.copy(), self.it)
 
 
+def ws_planes(p: Problem) -> int:
+    return DB_BASES if p.dictionary == "union" else p.J + 1
+
+
+def ws_analysis(p: Problem, x: np.ndarray) -> np.ndarray:
+    """W_s x for the problem's dictionary."""
+    return union_analysis(x, p.J) if p.dictionary == "union" else iuwt_analysis(x, p.J, p.gen)
+
+
+def ws_adjoint(p: Problem, u: np.ndarray) -> np.ndarray:
+    """W_s^T u for the problem's dictionary."""
+    return union_adjoint(u, p.J) if p.dictionary == "union" else iuwt_adjoint(u, p.J, p.gen)
+
+
 def zero_state(p: Problem) -> State:
     L, n, _ = p.shape
-    return State(np.zeros((L, n, n)), np.zeros((L, p.J + 1, n, n)), np.zeros((L, n, n)))
+    return State(np.zeros((L, n, n)), np.zeros((L, ws_planes(p), n, n)), np.zeros((L, n, n)))
 
 
 def iterate(p: Problem, s: State, n_iter: int = 1) -> State:
@@ -271,10 +402,10 @@ def iterate(p: Problem, s: State, n_iter: int = 1) -> State:
     X, U, V = s.X, s.U, s.V
     for _ in range(n_iter):
         grad = gradient(X, p.y, p.hhat, p.w)
-        spatial = p.mu_s * iuwt_adjoint(U, p.J, p.gen)
+        spatial = p.mu_s * ws_adjoint(p, U)
         spectral = p.mu_l * spectral_adjoint(V)
         Xt = positive(X - p.tau * (grad + spatial + spectral))
-        Ut = sat(U + p.sigma * p.mu_s * iuwt_analysis(2.0 * Xt - X, p.J, p.gen))
+        Ut = sat(U + p.sigma * p.mu_s * ws_analysis(p, 2.0 * Xt - X))
         Vt = sat(V + p.sigma * p.mu_l * spectral_analysis(2.0 * Xt - X))
         X = p.rho * Xt + (1.0 - p.rho) * X
         U = p.rho * Ut + (1.0 - p.rho) * U
@@ -290,7 +421,7 @@ def objective_terms(p: Problem, X: np.ndarray) -> tuple[float, float, float]:
     """
     r = p.y - apply_H(X, p.hhat)
     data = 0.5 * float(np.sum(p.w[:, None, None] * r * r))
-    spatial = p.mu_s * float(np.sum(np.abs(iuwt_analysis(X, p.J, p.gen))))
+    spatial = p.mu_s * float(np.sum(np.abs(ws_analysis(p, X))))
     spectral = p.mu_l * float(np.sum(np.abs(spectral_analysis(X))))
     return data, spatial, spectral
 
@@ -352,15 +483,25 @@ def condat_steps(beta: float, l_norm2: float, sigma: float = 1.0, safety: float 
     return tau, sigma, rho, delta
 
 
+def union_norm2(n: int, J: int, n_iter: int = 30, seed: int = 7) -> float:
+    """||W_s||^2 of the union of bases by the power method (1 for a tight frame)."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    x0 = rng.standard_normal((1, n, n))
+    return power_iteration(lambda v: union_adjoint(union_analysis(v, J), J), x0, n_iter)
+
+
 def make_problem(y, psf, J, gen=1, mu_s=0.25, mu_l=3.0, sigma=1.0, rho=1.0, w=None,
-                 tau=None, margin=1.01, power_iters=50) -> Problem:
+                 tau=None, margin=1.01, power_iters=50, dictionary="iuwt") -> Problem:
     """Problem with step sizes from power-iteration norms (x margin) and Condat."""
     y = np.asarray(y, dtype=np.float64)
     hhat = psf_multiplier(psf)
     w = np.ones(y.shape[0]) if w is None else np.asarray(w, dtype=np.float64)
     if tau is None:
         beta = margin * data_lipschitz(hhat, w, power_iters)
-        wn = margin * iuwt_norm2(y.shape[-1], J, gen)
+        if dictionary == "union":
+            wn = margin * union_norm2(y.shape[-1], J)
+        else:
+            wn = margin * iuwt_norm2(y.shape[-1], J, gen)
         tau, sigma, rho, _ = condat_steps(beta, dual_norm2(mu_s, mu_l, wn), sigma, rho=rho)
     return Problem(y=y, hhat=hhat, J=J, gen=gen, mu_s=mu_s, mu_l=mu_l, tau=tau,
-                   sigma=sigma, rho=rho, w=w)
+                   sigma=sigma, rho=rho, w=w, dictionary=dictionary)

@@ -3,7 +3,7 @@
 Each fixture holds the minimiser of Eq. 5 + Eq. 6 for one 8 x 8 x 2 case of
 tiny_problem.py, found by the dense ADMM of oracle/dense.py and confirmed by
 the smoothed projected-gradient brute force of the same module (they must
-agree to 1e-6).  Run:  python tests/golden/make_tiny_minimizer.py
+agree to 1e-6).  Run:  python tests/golden/make_tiny_minimizer.py [case ...]
 """
 import json
 import os
@@ -22,8 +22,12 @@ from tiny_problem import tiny_inputs, CASES  # noqa: E402
 
 def main():
     y, psf, _ = tiny_inputs()
+    only = sys.argv[1:]
     for name, c in CASES.items():
-        p = mo.make_problem(y, psf, c["J"], gen=c["gen"], mu_s=c["mu_s"], mu_l=c["mu_l"], tau=1.0)
+        if only and name not in only:
+            continue
+        p = mo.make_problem(y, psf, c["J"], gen=c["gen"], mu_s=c["mu_s"], mu_l=c["mu_l"], tau=1.0,
+                            dictionary=c.get("dictionary", "iuwt"))
         ops = dense.dense_operators(p)
         x_admm = dense.admm_minimize(p, 12000, 1.0, ops)
         x_pg = dense.smoothed_projected_gradient(p, ops)

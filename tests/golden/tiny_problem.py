@@ -26,4 +26,5 @@ def tiny_inputs(seed: int = 5):
 CASES = {
     "gen1_J1": dict(J=1, gen=1, mu_s=0.05, mu_l=0.05),
     "gen2_J1": dict(J=1, gen=2, mu_s=0.03, mu_l=0.08),
+    "union_J2": dict(J=2, gen=1, mu_s=0.01, mu_l=0.02, dictionary="union"),
 }

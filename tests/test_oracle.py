@@ -233,12 +233,15 @@ def test_algorithm1_reaches_independent_minimiser(case):
         g = json.load(f)
     c = g["case"]
     y, psf, _ = tiny_inputs()
-    p = mo.make_problem(y, psf, c["J"], gen=c["gen"], mu_s=c["mu_s"], mu_l=c["mu_l"], tau=1.0)
+    dic = c.get("dictionary", "iuwt")
+    p = mo.make_problem(y, psf, c["J"], gen=c["gen"], mu_s=c["mu_s"], mu_l=c["mu_l"], tau=1.0, dictionary=dic)
     beta = float(np.max(np.abs(p.hhat) ** 2))
-    l2 = mo.dual_norm2(p.mu_s, p.mu_l, mo.iuwt_norm2_closed_form(8, p.J, p.gen))
+    ws2 = 1.0 if dic == "union" else mo.iuwt_norm2_closed_form(8, p.J, p.gen)   # the union is a tight frame
+    l2 = mo.dual_norm2(p.mu_s, p.mu_l, ws2)
     p.tau = 1.0 / beta
     p.sigma = 0.9 * (1.0 / p.tau - beta / 2) / l2          # Condat: 1/tau - sigma ||L||^2 > beta/2
-    s = mo.iterate(p, mo.zero_state(p), 4000)
+    # the union's eight bases give 8x more dual coefficients, which converge more slowly
+    s = mo.iterate(p, mo.zero_state(p), 12000 if dic == "union" else 4000)
     x_ref = np.array(g["x"])
     assert np.linalg.norm(s.X.ravel() - x_ref) / np.linalg.norm(x_ref) < 1e-6
     assert abs(mo.objective(p, s.X) - g["objective"]) / g["objective"] < 1e-9
@@ -302,6 +305,108 @@ def test_objective_special_cases():
 def test_snr_definition():
     X = rnd((2, 8, 8), 22)
     assert abs(mo.snr_db(0.9 * X, X) - 20.0) < 1e-12
+
+
+# ---------------------------------------------------------------- W_s as a union of Daubechies bases (Sec. 4)
+
+@pytest.mark.parametrize("p", range(1, 9))
+def test_daubechies_filter_definition(p):
+    """Sum sqrt(2), orthonormal even shifts, p vanishing moments of the mirror filter."""
+    h = mo.daubechies_lowpass(p)
+    t = np.arange(h.size)
+    assert h.size == 2 * p
+    assert abs(h.sum() - np.sqrt(2.0)) < 1e-12
+    for m in range(p):
+        assert abs(np.dot(h[:h.size - 2 * m], h[2 * m:]) - (1.0 if m == 0 else 0.0)) < 1e-12
+    g = mo.daubechies_highpass(h)
+    for m in range(p):
+        assert abs(np.sum(t ** m * g)) <= 1e-12 * np.sum(t ** m * np.abs(g)) + 1e-14
+
+
+def test_daubechies_closed_forms():
+    assert np.allclose(mo.daubechies_lowpass(1), [2 ** -0.5, 2 ** -0.5], rtol=0, atol=1e-15)
+    r3 = np.sqrt(3.0)
+    db2 = np.array([1 + r3, 3 + r3, 3 - r3, 1 - r3]) / (4 * np.sqrt(2.0))
+    assert np.allclose(mo.daubechies_lowpass(2), db2, rtol=0, atol=1e-15)
+
+
+@pytest.mark.parametrize("p", [1, 2, 5, 8])
+@pytest.mark.parametrize("n,J", [(8, 2), (16, 3), (32, 1)])
+def test_dwt2_orthogonal_and_adjoint(p, n, J):
+    """The periodised filter bank is orthonormal at every level, including
+    levels shorter than the filter (db8 at 4 x 4 wraps around)."""
+    h = mo.daubechies_lowpass(p)
+    x = rnd((2, n, n), 30 + p)
+    u = rnd((2, n, n), 40 + p)
+    c = mo.dwt2(x, h, J)
+    assert abs(np.linalg.norm(c) - np.linalg.norm(x)) < 1e-12 * np.linalg.norm(x)
+    assert abs(np.vdot(c, u) - np.vdot(x, mo.dwt2_adjoint(u, h, J))) < 1e-12 * n * n
+    assert np.max(np.abs(mo.dwt2_adjoint(c, h, J) - x)) < 1e-12
+
+
+def test_haar_level_on_two_by_two_blocks():
+    """Haar (p = 1), one level: block [[a, b], [c, d]] gives (a+b+c+d)/2 (top-left
+    quadrant), (a-b+c-d)/2 (top-right), (a+b-c-d)/2 (bottom-left), (a-b-c+d)/2."""
+    x = rnd((1, 8, 8), 50)
+    c = mo.dwt2(x, mo.daubechies_lowpass(1), 1)[0]
+    a, b, cc, d = x[0, 0::2, 0::2], x[0, 0::2, 1::2], x[0, 1::2, 0::2], x[0, 1::2, 1::2]
+    assert np.allclose(c[:4, :4], (a + b + cc + d) / 2, atol=1e-14)
+    assert np.allclose(c[:4, 4:], (a - b + cc - d) / 2, atol=1e-14)
+    assert np.allclose(c[4:, :4], (a + b - cc - d) / 2, atol=1e-14)
+    assert np.allclose(c[4:, 4:], (a - b - cc + d) / 2, atol=1e-14)
+
+
+@pytest.mark.parametrize("p", [1, 3, 8])
+def test_constant_image_has_only_coarse_coefficients(p):
+    """Every detail filter kills constants; each level multiplies DC by 2 (sqrt 2 per axis)."""
+    n, J = 16, 3
+    c = mo.dwt2(np.full((1, n, n), 0.7), mo.daubechies_lowpass(p), J)[0]
+    m = n >> J
+    assert np.allclose(c[:m, :m], 0.7 * 2 ** J, atol=1e-12)
+    c[:m, :m] = 0.0
+    assert np.max(np.abs(c)) < 1e-12
+
+
+def test_union_of_bases_is_a_tight_frame():
+    x = rnd((2, 16, 16), 60)
+    w = mo.union_analysis(x, 3)
+    assert w.shape == (2, 8, 16, 16)
+    assert abs(np.linalg.norm(w) - np.linalg.norm(x)) < 1e-12 * np.linalg.norm(x)
+    assert np.max(np.abs(mo.union_adjoint(w, 3) - x)) < 1e-12
+    u = rnd((2, 8, 16, 16), 61)
+    assert abs(np.vdot(w, u) - np.vdot(x, mo.union_adjoint(u, 3))) < 1e-11
+    assert abs(mo.union_norm2(16, 3) - 1.0) < 1e-12
+    # the eight bases differ: the union is redundant, not eight copies of one basis
+    assert np.linalg.norm(w[:, 0] - w[:, 1]) > 0.1 * np.linalg.norm(w[:, 0])
+
+
+def test_planted_mirror_filter_mistake_is_caught(monkeypatch):
+    """A highpass without the alternating sign is not orthogonal to the lowpass."""
+    mo._step_matrices.cache_clear()          # the step matrices are built from the filters
+    monkeypatch.setattr(mo, "daubechies_highpass", lambda h: h[::-1].copy())
+    x = rnd((1, 16, 16), 62)
+    c = mo.dwt2(x, mo.daubechies_lowpass(3), 2)
+    mo._step_matrices.cache_clear()
+    assert abs(np.linalg.norm(c) - np.linalg.norm(x)) > 1e-3 * np.linalg.norm(x)
+
+
+def test_successive_differences_shrink_in_condat_metric_union():
+    y, psf, _ = tiny_inputs()
+    p = mo.make_problem(y, psf, 2, mu_s=0.01, mu_l=0.02, tau=1.0, dictionary="union")
+    beta = float(np.max(np.abs(p.hhat) ** 2))
+    p.tau = 0.5 / beta
+    p.sigma = 0.9 * (1.0 / p.tau - beta / 2) / mo.dual_norm2(p.mu_s, p.mu_l, 1.0)
+    s = mo.zero_state(p)
+    prev, first = None, None
+    for _ in range(200):
+        s2 = mo.iterate(p, s, 1)
+        dx, du, dv = s2.X - s.X, s2.U - s.U, s2.V - s.V
+        cross = p.mu_s * np.vdot(mo.union_analysis(dx, p.J), du) + p.mu_l * np.vdot(mo.spectral_analysis(dx), dv)
+        d = np.vdot(dx, dx) / p.tau + (np.vdot(du, du) + np.vdot(dv, dv)) / p.sigma - 2.0 * cross
+        first = d if first is None else first
+        if prev is not None and d > 1e-18 * first:
+            assert d <= prev * (1 + 1e-9)
+        prev, s = d, s2
 
 
 # ---------------------------------------------------------------- the pins catch planted mistakes
