@@ -10,6 +10,11 @@
  * with H_l the circular convolution by the PSF of channel l (Eq. 4), W_s the
  * isotropic undecimated wavelet transform (B3 spline, J detail planes plus the
  * coarse plane, periodic) and W_lambda the orthonormal DCT-II along channels.
+ * W_s may instead be the union of eight orthonormal Daubechies wavelet bases
+ * the paper compares it with (Sec. 4): W_s x = (1/sqrt 8)[Psi_1 x; ..; Psi_8 x],
+ * Psi_p the J-level periodic 2D DWT with the filter of p vanishing moments
+ * (minimum phase, by spectral factorisation), coefficients of each basis in
+ * the Mallat layout of an N x N plane; then U is [L][8][N][N].
  *
  * Conventions shared by every entry point:
  *  - Cubes are float32, channel-major, row-major: element (l, y, x) of an
@@ -62,6 +67,8 @@ typedef struct {
   const double* h_chan_weight; /* host, L weights w_l = 1/sigma_l^2 of Eq. 5; NULL: all 1 */
   int fine_levels;       /* tiling split j1 of W_s (advanced); < 0: automatic */
   int power_iters;       /* power-method passes for each operator norm; <= 0: 40 */
+  int dictionary;        /* W_s: 0 IUWT (above), 1 union of eight Daubechies bases (needs J >= 1;
+                            iuwt_gen and fine_levels are then ignored) */
 } muffin_params;
 
 /* Bytes of device workspace a context with these parameters needs (0 if the
@@ -120,7 +127,8 @@ int muffin_step_sizes(const muffin_ctx* ctx, double* tau, double* sigma, double*
 
 /* Per-stage timing: run n_iter passes launching each kernel stage between
  * CUDA events on the context stream (no graph); h_ms[k] receives the summed
- * milliseconds of stage k for k < n_stages (see muffin_stage_name).
+ * milliseconds of stage k for k < n_stages (see muffin_stage_name; with the
+ * union of bases, stage 0 is its adjoint and stage 4 its analysis).
  * Synchronises. */
 int muffin_iterate_timed(muffin_ctx* ctx, int n_iter, double* h_ms, int n_stages);
 int muffin_num_stages(void);
@@ -136,6 +144,12 @@ int muffin_kernels_per_iteration(const muffin_ctx* ctx);
 int muffin_tiling(const muffin_ctx* ctx, int* fine_levels, int* cluster);
 
 const char* muffin_last_error(const muffin_ctx* ctx);  /* ctx may be NULL (init errors) */
+
+/* The Daubechies lowpass filter with p vanishing moments (1 <= p <= 8) that
+ * the union of bases uses, h[0 .. 2p-1] (host, double), H(z) = sum_t h[t] z^-t,
+ * minimum phase, sum h = sqrt 2.  Host computation only (no CUDA call);
+ * returns 0, or -1 if p is out of range. */
+int muffin_daubechies_filter(int p, double* h_out);
 
 /* Batches of cubes of uneven sizes.  A batch captures one pass of Algorithm 1
  * of every context (each with its own sizes, PSFs, tiling and workspace) as

@@ -14,6 +14,7 @@ struct Geom {
   int gen;      // IUWT generation (1 or 2)
   int j1;       // fine levels computed on halo tiles; levels >= j1 run class-permuted
   int cs;       // blocks per cluster of the coarse kernel (0: single-block streaming kernel)
+  int dict = 0; // W_s: 0 IUWT, 1 union of eight Daubechies bases (k_dwt.cu)
 };
 
 // ---- FFT path (k_fft.cu) ----
@@ -71,6 +72,29 @@ cudaError_t launch_coarse(const Geom& g, const float* c_in, float* r_out, float*
 // Opt the wavelet kernels into shared memory and pick g.cs for this device.
 cudaError_t iuwt_configure(Geom& g);
 cudaError_t fft_configure(int n);
+
+// ---- W_s as a union of eight orthonormal Daubechies bases (k_dwt.cu) ----
+constexpr int kDbBases = 8;
+// Daubechies lowpass filter with p vanishing moments (1 <= p <= 8), 2p taps,
+// by spectral factorisation (host, double precision); false if p is out of range.
+bool daubechies_lowpass(int p, double* h);
+struct DwtArgs {
+  const float* src;  // analysis input [L][N][N] (shared by the bases)
+  float* U;          // coefficients / duals [L][8][N][N], Mallat layout per basis
+  float* W1;         // scratch [L][8][N][N]
+  float* W2;         // scratch [L][8][N][N]
+  float* S;          // adjoint output [L][N][N]
+  float k;           // sigma * mu_s (update mode)
+  float rho;
+};
+// Upload the filters once per process and device.
+cudaError_t dwt_configure();
+// mode MODE_UPDATE: U <- rho sat(U + k W_s src) + (1 - rho) U; MODE_LINEAR: U = W_s src.
+cudaError_t launch_dwt_analysis(const Geom& g, const DwtArgs& a, int mode, cudaStream_t s);
+// S = W_s^T U.
+cudaError_t launch_dwt_adjoint(const Geom& g, const DwtArgs& a, cudaStream_t s);
+// sum |x| over n floats -> one partial per block (at most 1024).
+cudaError_t launch_abs_sum(const float* x, size_t n, double* partials, int* nparts, cudaStream_t s);
 
 // ---- spectral step (k_spectral.cu) ----
 enum SpecMode { SPEC_UPDATE = 0, SPEC_NORM = 1, SPEC_TONLY = 2 };

@@ -62,6 +62,8 @@ int check(const muffin_params* p, std::string* why) {
   if (p->nchan < 1 || p->nchan > 512) return fail("nchan must be in [1, 512]");
   if (p->nscales < 0 || (1 << p->nscales) >= p->nx) return fail("nscales J must satisfy 0 <= J and 2^J < N");
   if (p->iuwt_gen != 1 && p->iuwt_gen != 2) return fail("iuwt_gen must be 1 or 2");
+  if (p->dictionary != 0 && p->dictionary != 1) return fail("dictionary must be 0 (IUWT) or 1 (union of bases)");
+  if (p->dictionary == 1 && p->nscales < 1) return fail("the union of bases needs nscales J >= 1 levels");
   if (!(p->mu_s >= 0.0) || !std::isfinite(p->mu_s) || !(p->mu_l >= 0.0) || !std::isfinite(p->mu_l))
     return fail("mu_s and mu_l must be finite and >= 0");
   if (!std::isfinite(p->tau) || !std::isfinite(p->sigma) || !std::isfinite(p->rho)) return fail("non-finite step size");
@@ -70,6 +72,7 @@ int check(const muffin_params* p, std::string* why) {
     for (int l = 0; l < p->nchan; ++l)
       if (!(p->h_chan_weight[l] > 0.0) || !std::isfinite(p->h_chan_weight[l])) return fail("channel weights must be finite and > 0");
   }
+  if (p->dictionary == 1) return MUFFIN_OK;   // no wavelet tiling to choose
   int j1 = p->fine_levels;
   if (j1 < 0) {
     j1 = auto_j1(p->nx, p->nscales, p->iuwt_gen);
@@ -86,6 +89,7 @@ int check(const muffin_params* p, std::string* why) {
 
 struct Layout {
   size_t X, U, V, y, b, Kp, Kb, spec, S, T, D, cr, hhat, yhat, z64, pw, partials, scal;
+  size_t W1, W2, W3;   // union of bases: [L][8][N][N] scratch each
   size_t twf, twd, twL, post, pre, invs, dense, w;
   size_t total;
   int max_parts;
@@ -95,11 +99,13 @@ struct Layout {
 Layout make_layout(const muffin_params* p) {
   Layout Lo{};
   const size_t n = p->nx, L = p->nchan, J = p->nscales, P = n * n;
-  Lo.j1 = p->fine_levels >= 0 ? p->fine_levels : auto_j1(p->nx, p->nscales, p->iuwt_gen);
+  const bool uni = p->dictionary == 1;
+  const size_t planes = uni ? (size_t)kDbBases : J + 1;
+  Lo.j1 = uni ? 0 : (p->fine_levels >= 0 ? p->fine_levels : auto_j1(p->nx, p->nscales, p->iuwt_gen));
   size_t off = 0;
   auto take = [&](size_t bytes) { off = (off + 255) & ~(size_t)255; const size_t o = off; off += bytes; return o; };
   Lo.X = take(L * P * 4);
-  Lo.U = take(L * (J + 1) * P * 4);
+  Lo.U = take(L * planes * P * 4);
   Lo.V = take(L * P * 4);
   Lo.y = take(L * P * 4);
   Lo.b = take(L * P * 4);
@@ -113,7 +119,10 @@ Layout make_layout(const muffin_params* p) {
   Lo.hhat = take(L * P * 16);
   Lo.yhat = take(L * P * 16);
   Lo.z64 = take(L * P * 16);
-  Lo.pw = take((J + 4) * P * 4);
+  Lo.pw = take((uni ? 2 + 3 * (size_t)kDbBases : J + 4) * P * 4);
+  Lo.W1 = take(uni ? L * kDbBases * P * 4 : 0);
+  Lo.W2 = take(uni ? L * kDbBases * P * 4 : 0);
+  Lo.W3 = take(uni ? L * kDbBases * P * 4 : 0);
   size_t mp = 1024;
   mp = std::max(mp, (n / 64) * (n / 64) * L);
   mp = std::max(mp, (size_t)64 * 8 * L);   // coarse blocks for any split j1 <= 3 and cluster <= 8
@@ -166,7 +175,19 @@ struct muffin_ctx {
   double* partials() const { return at<double>(lo.partials); }
   double* scal() const { return at<double>(lo.scal); }
   // W_s^T U as the primal step reads it
-  const float* S_ptr() const { return g.J == 0 ? U() : at<float>(lo.S); }
+  const float* S_ptr() const { return (g.J == 0 && g.dict == 0) ? U() : at<float>(lo.S); }
+  size_t planes() const { return g.dict ? (size_t)kDbBases : (size_t)g.J + 1; }
+  DwtArgs dwt(const float* src) const {
+    DwtArgs d{};
+    d.src = src;
+    d.U = U();
+    d.W1 = at<float>(lo.W1);
+    d.W2 = at<float>(lo.W2);
+    d.S = at<float>(lo.S);
+    d.k = (float)(sigma * mu_s);
+    d.rho = (float)rho;
+    return d;
+  }
 };
 
 #define CK(call)                                                                       \
@@ -223,7 +244,10 @@ static int enqueue_pass(muffin_ctx* ctx, cudaStream_t s, StageTimer* tm) {
   ia.rho = (float)ctx->rho;
   auto mark = [&](int k) { if (tm) tm->mark(k); };
   mark(-1);
-  if (spatial && g.J > 0 && g.j1 > 0) {
+  if (spatial && g.dict) {
+    CK(launch_dwt_adjoint(g, ctx->dwt(nullptr), s));
+    mark(0);
+  } else if (spatial && g.J > 0 && g.j1 > 0) {
     CK(launch_fine_adjoint(g, ia, s));
     mark(0);
   }
@@ -244,7 +268,10 @@ static int enqueue_pass(muffin_ctx* ctx, cudaStream_t s, StageTimer* tm) {
   pa.rho = (float)ctx->rho;
   CK(launch_rows_inv_primal(ctx->at<float>(lo.spec), pa, g.n, g.L, ctx->at<float>(lo.twf), s));
   mark(3);
-  if (spatial) {
+  if (spatial && g.dict) {
+    CK(launch_dwt_analysis(g, ctx->dwt(ctx->at<float>(lo.D)), MODE_UPDATE, s));
+    mark(4);
+  } else if (spatial) {
     if (g.j1 > 0 || g.J == 0) {
       CK(launch_fine_analysis(g, ia, MODE_UPDATE, s, nullptr));
       mark(4);
@@ -289,7 +316,9 @@ static int refresh_adjoints(muffin_ctx* ctx) {
   sa.dense = ctx->at<float>(lo.dense);
   sa.rho = 1.0f;
   CK(launch_spectral(sa, (int)ctx->P(), g.L, SPEC_TONLY, ctx->stream, nullptr));
-  if (g.J > g.j1) {
+  if (g.dict) {
+    CK(launch_dwt_adjoint(g, ctx->dwt(nullptr), ctx->stream));
+  } else if (g.J > g.j1) {
     float* rout = g.j1 > 0 ? ctx->at<float>(lo.cr) : ctx->at<float>(lo.S);
     CK(launch_coarse(g, nullptr, rout, ctx->U(), 0.f, 1.f, MODE_ADJ, nullptr, ctx->stream, nullptr));
   }
@@ -386,7 +415,7 @@ static int autotune_split(muffin_ctx* ctx) {
   cudaError_t e = iuwt_configure(ctx->g);
   if (e != cudaSuccess) return fail(ctx, MUFFIN_ERR_CUDA, "wavelet configuration", cudaGetErrorString(e));
   const Layout& lo = ctx->lo;
-  CK(cudaMemsetAsync(ctx->U(), 0, (size_t)ctx->vox() * (ctx->g.J + 1) * 4, ctx->stream));
+  CK(cudaMemsetAsync(ctx->U(), 0, (size_t)ctx->vox() * ctx->planes() * 4, ctx->stream));
   CK(cudaMemsetAsync(ctx->at<float>(lo.S), 0, ctx->vox() * 4, ctx->stream));
   CK(cudaMemsetAsync(ctx->at<float>(lo.cr), 0, ctx->vox() * 4, ctx->stream));
   return MUFFIN_OK;
@@ -424,7 +453,7 @@ int muffin_init(muffin_ctx** out, const muffin_params* p, const float* d_dirty, 
   ctx->p = *p;
   ctx->p.h_chan_weight = nullptr;
   ctx->lo = lo;
-  ctx->g = Geom{p->nx, p->nchan, p->nscales, p->iuwt_gen, lo.j1, 0};
+  ctx->g = Geom{p->nx, p->nchan, p->nscales, p->iuwt_gen, lo.j1, 0, p->dictionary};
   ctx->stream = stream;
   ctx->ws = reinterpret_cast<char*>(d_workspace);
   ctx->w.assign(p->nchan, 1.0);
@@ -434,13 +463,15 @@ int muffin_init(muffin_ctx** out, const muffin_params* p, const float* d_dirty, 
   ctx->sigma = p->sigma > 0 ? p->sigma : 1.0;
   ctx->rho = p->rho > 0 ? p->rho : 1.0;
   ctx->tau_auto = !(p->tau > 0);
-  ctx->split_auto = p->fine_levels < 0 && p->nscales > 0 && getenv("MUFFIN_NO_AUTOTUNE") == nullptr;
+  ctx->split_auto = p->dictionary == 0 && p->fine_levels < 0 && p->nscales > 0 &&
+                    getenv("MUFFIN_NO_AUTOTUNE") == nullptr;
   ctx->tau = p->tau > 0 ? p->tau : 0.0;
   if (ctx->p.power_iters <= 0) ctx->p.power_iters = 40;
   auto bail = [&](int code) { if (ctx->cap) cudaStreamDestroy(ctx->cap); g_init_error = ctx->err; delete ctx; return code; };
   cudaError_t e;
   if ((e = cudaStreamCreateWithFlags(&ctx->cap, cudaStreamNonBlocking))) { fail(ctx, MUFFIN_ERR_CUDA, "cudaStreamCreate", cudaGetErrorString(e)); return bail(MUFFIN_ERR_CUDA); }
-  if ((e = fft_configure(ctx->g.n)) || (e = iuwt_configure(ctx->g)) || (e = spectral_configure(ctx->g.L))) {
+  if ((e = fft_configure(ctx->g.n)) || (ctx->g.dict == 0 && (e = iuwt_configure(ctx->g))) ||
+      (ctx->g.dict == 1 && (e = dwt_configure())) || (e = spectral_configure(ctx->g.L))) {
     fail(ctx, MUFFIN_ERR_CUDA, "kernel configuration", cudaGetErrorString(e));
     return bail(MUFFIN_ERR_CUDA);
   }
@@ -531,7 +562,34 @@ int muffin_set_psf(muffin_ctx* ctx, const float* d_psf) {
     std::swap(pv, pw);
   }
   // ||W_s||^2: power method on W_s^T W_s over one N x N plane
-  if (g.J > 0) {
+  if (g.dict) {
+    Geom g1 = g;
+    g1.L = 1;
+    float* x = ctx->at<float>(lo.pw);
+    DwtArgs da{};
+    da.src = x;
+    da.U = x + P;
+    da.S = da.U + (size_t)kDbBases * P;
+    da.W1 = da.S + P;
+    da.W2 = da.W1 + (size_t)kDbBases * P;
+    da.k = 1.f;
+    da.rho = 1.f;
+    float* St = da.S;
+    CK(launch_fill_random(x, P, 0x5eed2ULL, s));
+    CK(launch_dot(x, x, P, ctx->partials(), &np, s));
+    CK(launch_sum_partials(ctx->partials(), np, sc + 4, s));
+    CK(launch_scale(x, P, nullptr, sc + 4, s));
+    for (int it = 0; it < ctx->p.power_iters; ++it) {
+      CK(launch_dwt_analysis(g1, da, MODE_LINEAR, s));
+      CK(launch_dwt_adjoint(g1, da, s));
+      CK(launch_dot(x, St, P, ctx->partials(), &np, s));
+      CK(launch_sum_partials(ctx->partials(), np, sc + 3, s));
+      CK(launch_dot(St, St, P, ctx->partials(), &np, s));
+      CK(launch_sum_partials(ctx->partials(), np, sc + 4, s));
+      CK(cudaMemcpyAsync(x, St, P * 4, cudaMemcpyDeviceToDevice, s));
+      CK(launch_scale(x, P, nullptr, sc + 4, s));
+    }
+  } else if (g.J > 0) {
     Geom g1 = g;
     g1.L = 1;
     float* x = ctx->at<float>(lo.pw);
@@ -634,11 +692,17 @@ int muffin_objective(muffin_ctx* ctx, double* h_obj, double* h_terms) {
   ia.U = ctx->U();
   ia.cr = ctx->at<float>(lo.D);   // c_{j1} of X goes to scratch, not to the state
   ia.partials = ctx->partials();
-  if (g.j1 > 0 || g.J == 0) {
+  if (g.dict) {
+    DwtArgs da = ctx->dwt(ctx->X());
+    da.U = ctx->at<float>(lo.W3);      // W_s X into scratch, not into the state
+    CK(launch_dwt_analysis(g, da, MODE_LINEAR, s));
+    CK(launch_abs_sum(da.U, (size_t)kDbBases * ctx->vox(), ctx->partials(), &np, s));
+    CK(launch_sum_partials(ctx->partials(), np, sc + 11, s));
+  } else if (g.j1 > 0 || g.J == 0) {
     CK(launch_fine_analysis(g, ia, MODE_NORM, s, &np));
     CK(launch_sum_partials(ctx->partials(), np, sc + 11, s));
   }
-  if (g.J > g.j1) {
+  if (!g.dict && g.J > g.j1) {
     const float* cin = g.j1 > 0 ? ctx->at<float>(lo.D) : ctx->X();
     CK(launch_coarse(g, cin, nullptr, ctx->U(), 0.f, 1.f, MODE_NORM, ctx->partials(), s, &np));
     CK(launch_sum_partials(ctx->partials(), np, sc + 12, s));
@@ -679,7 +743,8 @@ int muffin_get_state(muffin_ctx* ctx, float* d_x, float* d_u, float* d_v, long l
   if (!ctx || !d_x || !d_u || !d_v) return fail(ctx, MUFFIN_ERR_ARG, "NULL argument");
   const Geom& g = ctx->g;
   CK(cudaMemcpyAsync(d_x, ctx->X(), ctx->vox() * 4, cudaMemcpyDeviceToDevice, ctx->stream));
-  CK(launch_permute_planes(ctx->U(), d_u, g.n, g.L, g.J, g.j1, 0, ctx->stream));
+  if (g.dict) CK(cudaMemcpyAsync(d_u, ctx->U(), ctx->vox() * kDbBases * 4, cudaMemcpyDeviceToDevice, ctx->stream));
+  else CK(launch_permute_planes(ctx->U(), d_u, g.n, g.L, g.J, g.j1, 0, ctx->stream));
   CK(cudaMemcpyAsync(d_v, ctx->V(), ctx->vox() * 4, cudaMemcpyDeviceToDevice, ctx->stream));
   if (h_iter) *h_iter = ctx->iter;
   return MUFFIN_OK;
@@ -690,7 +755,8 @@ int muffin_set_state(muffin_ctx* ctx, const float* d_x, const float* d_u, const 
   if (ctx->state < 1) return fail(ctx, MUFFIN_ERR_STATE, "muffin_set_psf must come before muffin_set_state");
   const Geom& g = ctx->g;
   CK(cudaMemcpyAsync(ctx->X(), d_x, ctx->vox() * 4, cudaMemcpyDeviceToDevice, ctx->stream));
-  CK(launch_permute_planes(d_u, ctx->U(), g.n, g.L, g.J, g.j1, 1, ctx->stream));
+  if (g.dict) CK(cudaMemcpyAsync(ctx->U(), d_u, ctx->vox() * kDbBases * 4, cudaMemcpyDeviceToDevice, ctx->stream));
+  else CK(launch_permute_planes(d_u, ctx->U(), g.n, g.L, g.J, g.j1, 1, ctx->stream));
   CK(cudaMemcpyAsync(ctx->V(), d_v, ctx->vox() * 4, cudaMemcpyDeviceToDevice, ctx->stream));
   const int r = refresh_adjoints(ctx);
   if (r != MUFFIN_OK) return r;
@@ -732,6 +798,15 @@ double muffin_stage_bytes(const muffin_ctx* ctx, int k) {
   const Geom& g = ctx->g;
   const double V = (double)ctx->vox();
   const bool sp = ctx->mu_s != 0.0, sl = ctx->mu_l != 0.0;
+  if (g.dict) {
+    // union of bases: the adjoint reads the eight planes of U and writes
+    // W_s^T U once; the analysis reads D and reads and writes U
+    switch (k) {
+      case 0: return sp ? V * (4.0 * kDbBases + 4.0) : 0.0;
+      case 4: return sp ? V * (4.0 + 8.0 * kDbBases) : 0.0;
+      case 5: return 0.0;
+    }
+  }
   switch (k) {
     case 0: return (sp && g.J > 0 && g.j1 > 0) ? 4.0 * V * (g.j1 + 2) : 0.0;
     case 1: return 8.0 * V;
@@ -750,6 +825,7 @@ int muffin_kernels_per_iteration(const muffin_ctx* ctx) {
   if (!ctx) return 0;
   int n = 0;
   for (int k = 0; k < kNumStages; ++k) n += muffin_stage_bytes(ctx, k) > 0 ? 1 : 0;
+  if (ctx->g.dict && ctx->mu_s != 0.0) n += 4 * ctx->g.J - 1;   // 2J + 1 adjoint and 2J analysis kernels, not 2
   return n;
 }
 

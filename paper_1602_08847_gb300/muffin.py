@@ -32,7 +32,7 @@ class muffin_params(ctypes.Structure):
         ("iuwt_gen", ctypes.c_int), ("mu_s", ctypes.c_double), ("mu_l", ctypes.c_double),
         ("tau", ctypes.c_double), ("sigma", ctypes.c_double), ("rho", ctypes.c_double),
         ("h_chan_weight", ctypes.POINTER(ctypes.c_double)), ("fine_levels", ctypes.c_int),
-        ("power_iters", ctypes.c_int),
+        ("power_iters", ctypes.c_int), ("dictionary", ctypes.c_int),
     ]
 
 
@@ -61,6 +61,7 @@ def _load():
         "muffin_stage_bytes": (D, [P, I]),
         "muffin_kernels_per_iteration": (I, [P]),
         "muffin_tiling": (I, [P, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int)]),
+        "muffin_daubechies_filter": (I, [I, ctypes.POINTER(ctypes.c_double)]),
         "muffin_last_error": (ctypes.c_char_p, [P]),
         "muffin_batch_create": (I, [ctypes.POINTER(P), ctypes.POINTER(P), I, P]),
         "muffin_batch_iterate": (I, [P, I]),
@@ -87,8 +88,11 @@ def _stream() -> int:
     return torch.cuda.current_stream().cuda_stream
 
 
+DICTIONARIES = {"iuwt": 0, "union": 1}
+
+
 def make_params(n, nchan, nscales, gen=1, mu_s=0.25, mu_l=3.0, tau=0.0, sigma=0.0, rho=0.0, weights=None,
-                fine_levels=-1, power_iters=0):
+                fine_levels=-1, power_iters=0, dictionary="iuwt"):
     p = muffin_params()
     p.nx = p.ny = int(n)
     p.nchan, p.nscales, p.iuwt_gen = int(nchan), int(nscales), int(gen)
@@ -99,6 +103,7 @@ def make_params(n, nchan, nscales, gen=1, mu_s=0.25, mu_l=3.0, tau=0.0, sigma=0.
         p._w = arr
         p.h_chan_weight = ctypes.cast(arr, ctypes.POINTER(ctypes.c_double))
     p.fine_levels, p.power_iters = int(fine_levels), int(power_iters)
+    p.dictionary = DICTIONARIES[dictionary]
     return p
 
 
@@ -125,11 +130,14 @@ class Muffin:
 
     def __init__(self, dirty: torch.Tensor, psf: torch.Tensor | None = None, *, nscales: int, gen: int = 1,
                  mu_s: float = 0.25, mu_l: float = 3.0, tau: float = 0.0, sigma: float = 0.0, rho: float = 0.0,
-                 weights=None, fine_levels: int = -1, power_iters: int = 0, device="cuda"):
+                 weights=None, fine_levels: int = -1, power_iters: int = 0, dictionary: str = "iuwt", device="cuda"):
         L, n, n2 = dirty.shape
         self.shape = (L, n, n2)
         self.nscales = nscales
-        self.params = make_params(n, L, nscales, gen, mu_s, mu_l, tau, sigma, rho, weights, fine_levels, power_iters)
+        self.dictionary = dictionary
+        self.u_planes = 8 if dictionary == "union" else nscales + 1   # planes of the dual U per channel
+        self.params = make_params(n, L, nscales, gen, mu_s, mu_l, tau, sigma, rho, weights, fine_levels, power_iters,
+                                  dictionary)
         code, msg = muffin_check_params(self.params)
         if code != MUFFIN_OK:
             raise MuffinError(code, msg)
@@ -184,7 +192,7 @@ class Muffin:
         L, n, _ = self.shape
         dev = self.workspace.device
         x = torch.empty((L, n, n), dtype=torch.float32, device=dev)
-        u = torch.empty((L, self.nscales + 1, n, n), dtype=torch.float32, device=dev)
+        u = torch.empty((L, self.u_planes, n, n), dtype=torch.float32, device=dev)
         v = torch.empty((L, n, n), dtype=torch.float32, device=dev)
         it = ctypes.c_longlong()
         self._check(_lib.muffin_get_state(self._ctx, _ptr(x), _ptr(u), _ptr(v), ctypes.byref(it)))

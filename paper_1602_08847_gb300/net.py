@@ -247,8 +247,8 @@ def warm_start(problem, net: WarmStartNet, net_input: torch.Tensor, keep_state: 
     x, aux = net.predict(net_input)
     u = u0
     if aux is not None:
-        if aux.shape[1] != problem.nscales + 1:
-            raise ValueError(f"network gives {aux.shape[1]} fields, the problem has {problem.nscales + 1} planes of U")
+        if aux.shape[1] != problem.u_planes:
+            raise ValueError(f"network gives {aux.shape[1]} fields, the problem has {problem.u_planes} planes of U")
         u = aux
     problem.set_state(x, u, v0, it)
     f1, _ = problem.objective()

@@ -11,9 +11,9 @@ def small_cube(n, L, J, seed, n_src=6, n_ant=16):
     return synth.make_cube(synth.CubeConfig("t", n=n, nchan=L, n_src=n_src, n_ant=n_ant, nscales=J, seed=seed))
 
 
-def problem(cube, J, gen, mu_s, mu_l, tau=None, sigma=1.0, rho=1.0, w=None):
+def problem(cube, J, gen, mu_s, mu_l, tau=None, sigma=1.0, rho=1.0, w=None, dictionary="iuwt"):
     p = mo.make_problem(cube.dirty, cube.psf, J, gen=gen, mu_s=mu_s, mu_l=mu_l, sigma=sigma, rho=rho, w=w,
-                        tau=tau)
+                        tau=tau, dictionary=dictionary)
     return p
 
 
@@ -22,7 +22,7 @@ def gpu_solver(cube, p, fine_levels=-1, power_iters=0):
     return Muffin(torch.from_numpy(cube.dirty).cuda(), torch.from_numpy(cube.psf).cuda(), nscales=p.J, gen=p.gen,
                   mu_s=p.mu_s, mu_l=p.mu_l, tau=p.tau, sigma=p.sigma, rho=p.rho,
                   weights=None if np.all(p.w == 1.0) else list(p.w), fine_levels=fine_levels,
-                  power_iters=power_iters)
+                  power_iters=power_iters, dictionary=p.dictionary)
 
 
 def to64(t):
@@ -37,7 +37,7 @@ def max_rel(a, b):
 
 def random_state(p, seed):
     L, n, _ = p.shape
-    x, u, v = synth.random_state((L, n, n), p.J, seed, scale=float(np.abs(p.y).max()))
+    x, u, v = synth.random_state((L, n, n), mo.ws_planes(p) - 1, seed, scale=float(np.abs(p.y).max()))
     return x, u, v
 
 

@@ -101,3 +101,17 @@ def test_net_sizes_and_create_argument_checks(so):
     assert so.muffin_net_create(ctypes.byref(net), 4, 8, 8, 2, neg, 0, ctypes.c_void_p(256), 1 << 30, None) == -1
     assert so.muffin_net_create(ctypes.byref(net), 4, 8, 8, 1, None, 0, ctypes.c_void_p(256), 16, None) == -3
     assert not net.value
+
+
+def test_daubechies_filters_match_the_oracle(so):
+    """The library's own filters (host C++, Durand-Kerner roots) equal the
+    oracle's (numpy roots) for every basis of the union."""
+    import numpy as np
+    from oracle import muffin_oracle as mo
+    so.muffin_daubechies_filter.argtypes = [ctypes.c_int, ctypes.POINTER(ctypes.c_double)]
+    for p in range(1, 9):
+        buf = (ctypes.c_double * 16)()
+        assert so.muffin_daubechies_filter(p, buf) == 0
+        assert np.allclose(np.array(buf[:2 * p]), mo.daubechies_lowpass(p), rtol=0, atol=1e-12), p
+    assert so.muffin_daubechies_filter(0, (ctypes.c_double * 16)()) == -1
+    assert so.muffin_daubechies_filter(9, (ctypes.c_double * 16)()) == -1
