@@ -40,6 +40,7 @@ def parse():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-ttt", action="store_true")
     ap.add_argument("--no-batch", action="store_true")
+    ap.add_argument("--no-union", action="store_true")
     ap.add_argument("--fine-levels", type=int, default=-1,
                     help="wavelet split (levels on halo tiles); -1: chosen by timing at set-up")
     return ap.parse_args()
@@ -259,6 +260,31 @@ def main():
                                f"{args.steps} passes, D2H of X; one call"}
 
     # four uneven cubes advanced together: one graph launch per pass (muffin_batch) vs one by one
+    # the comparison dictionary of Sec. 4: the same pass with W_s = union of eight Daubechies bases
+    if not args.no_union and rank == 0:
+        cu = synth.make_cube("B")
+        mu = Muffin(torch.from_numpy(cu.dirty).cuda(), torch.from_numpy(cu.psf).cuda(), nscales=4,
+                    mu_s=0.25, mu_l=3.0, dictionary="union")
+        mi = Muffin(torch.from_numpy(cu.dirty).cuda(), torch.from_numpy(cu.psf).cuda(), nscales=4,
+                    mu_s=0.25, mu_l=3.0)
+        res = {}
+        for name, m_ in (("union", mu), ("iuwt", mi)):
+            m_.iterate(10)
+            torch.cuda.synchronize()
+            s0, s1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            s0.record()
+            m_.iterate(50)
+            s1.record()
+            torch.cuda.synchronize()
+            res[name] = s0.elapsed_time(s1) / 50
+        vox_b = cu.cfg.nchan * cu.cfg.n * cu.cfg.n
+        line["union_dictionary"] = {"workload": "256x256x64, J=4, W_s = union of 8 Daubechies bases (db1-db8)",
+                                    "ms_per_step": res["union"], "value": vox_b / (res["union"] * 1e-3),
+                                    "unit": METRIC, "iuwt_ms_per_step": res["iuwt"],
+                                    "kernels_per_step": mu.kernels_per_iteration()}
+        mu.close()
+        mi.close()
+
     if not args.no_batch and rank == 0:
         from paper_1602_08847_gb300.muffin import Batch
         ms = []
