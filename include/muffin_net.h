@@ -95,6 +95,12 @@ int muffin_net_train_step(muffin_net* net, const float* d_dirty, const float* d_
                           const void* d_target_aux, float lr, double* d_loss);
 
 const char* muffin_net_last_error(const muffin_net* net);  /* net may be NULL (create errors) */
+
+/* Number of tensor-core waits of the 32 -> 32 layers on the current device
+ * that gave up since the last call (a layer whose wait gives up leaves its
+ * remaining output tiles unwritten); resets the count.  Synchronises the
+ * device; -1 on a CUDA error. */
+int muffin_net_wait_timeouts(void);
 void muffin_net_destroy(muffin_net* net);
 
 /* ---- single layers (the kernels the network is made of), for callers that

@@ -13,14 +13,15 @@
 // at the same chunk then hit eight different bank groups, which keeps the
 // ldmatrix loads below free of conflicts.
 //
-// The 32 -> 32 layers are implicit GEMMs on the tensor cores
-// (mma.m16n8k16, bfloat16 in, float32 accumulate):
+// The 32 -> 32 layers are implicit GEMMs on the tensor cores, bfloat16 in,
+// float32 accumulate:
 //   forward      z[p][co]  = sum_tap sum_ci a[p + d(tap)][ci] W[tap][co][ci]
-//                 (M = voxels, N = co, K = 27 taps x 32 ci),
+//                 (M = voxels, N = co, K = 27 taps x 32 ci), tcgen05.mma with the
+//                 accumulator in tensor memory,
 //   input grad   da[p][ci] = sum_tap sum_co dz[p - d(tap)][co] W[tap][co][ci],
 //                 the same kernel on the flipped, transposed weights,
 //   weight grad  dW[tap][co][ci] = sum_p dz[p][co] a[p + d(tap)][ci]
-//                 (M = co, N = ci, K = voxels), one warp per tap.
+//                 (M = co, N = ci, K = voxels), warp-level mma.m16n8k16, one warp per tap.
 // The 1 -> 32 and 32 -> K layers are 27 or 864 multiply-adds per voxel and
 // output; they run on the CUDA cores.  Every reduction over voxels is a
 // per-block partial sum followed by a fixed-order sum: results do not depend
@@ -55,7 +56,6 @@ constexpr int kMaxOut = 8;                   // output maps of the last layer, a
 constexpr int kMaxPart = 512;                // cap of per-block partial slots (weight gradients)
 constexpr int kMaxLossPart = 1024;
 
-constexpr int conv_smem = NTAP * C * ROWB + HV * ROWB;      // 55296 + 46080
 
 struct Dims {
   int nz, ny, nx;
@@ -87,11 +87,6 @@ __device__ __forceinline__ void cp_async16(uint32_t dst, const void* src, int sr
 
 __device__ __forceinline__ void cp_async_wait_all() {
   asm volatile("cp.async.commit_group;\ncp.async.wait_group 0;\n" ::: "memory");
-}
-
-__device__ __forceinline__ void ldsm_x4(uint32_t addr, uint32_t& r0, uint32_t& r1, uint32_t& r2, uint32_t& r3) {
-  asm volatile("ldmatrix.sync.aligned.m8n8.x4.shared.b16 {%0,%1,%2,%3}, [%4];\n"
-               : "=r"(r0), "=r"(r1), "=r"(r2), "=r"(r3) : "r"(addr));
 }
 
 __device__ __forceinline__ void ldsm_x4_t(uint32_t addr, uint32_t& r0, uint32_t& r1, uint32_t& r2, uint32_t& r3) {
@@ -187,108 +182,186 @@ __device__ __forceinline__ uint4 pack8(const float* f) {
 
 enum { EPI_RELU = 0, EPI_BIAS = 1, EPI_MASK = 2 };
 
-// out = epilogue(sum_tap sum_k in[p + d(tap)][k] wk[tap][n][k]); wk rows n hold
-// the 32 reduction features contiguously.  EPI_RELU / EPI_BIAS add bias[n]
-// (bias may be null) and EPI_RELU clamps at 0; EPI_MASK zeroes outputs whose
-// mask entry is not > 0 (mask may be null).  Persistent: each block loads the
-// weights once and walks tiles with stride gridDim.x.  8 warps; warp w owns
-// output rows 2w and 2w+1 of the tile (16 voxels each).
+// ------------------------------------------------------------------ 32 -> 32 layers on tcgen05 (UMMA)
+//
+// One CTA of 128 threads owns 128 output voxels at a time (one channel, 16
+// rows, 8 columns): D[128 voxels][32 features] accumulates in tensor memory
+// over 27 taps x 2 steps of K = 16 by tcgen05.mma (kind::f16, bfloat16 A and
+// B, float32 D, M = 128, N = 32), both operands read from shared memory
+// through matrix descriptors in the canonical K-major layout without swizzle:
+// 8-row x 16-byte core matrices.  The halo tile (3 x 18 x 10 voxels) is stored
+// feature-chunk major, so the 8 consecutive voxels of one output row are one
+// core matrix in every tap's shifted window: rows of a window are 16 B apart,
+// the next output row (next 8-row group) is one halo row (160 B) further, and
+// the next 8 input features are one chunk plane (8640 B) further.  Weights are
+// stored [tap][chunk][co][16 B]: next 8 outputs 128 B, next 8 inputs 512 B.
+// Thread 0 issues the 54 MMAs and commits them to an mbarrier; every warp then
+// reads its 32 TMEM lanes (tcgen05.ld 32x32b.x32) for the epilogue.  Waits on
+// the mbarrier are bounded: on timeout the CTA records it in g_tc_timeouts,
+// skips the rest of its tiles and still frees its tensor memory.
+constexpr int U_TY = 16, U_TX = 8;                          // output tile: 16 rows x 8 columns, one channel
+constexpr int U_HY = U_TY + 2, U_HX = U_TX + 2;             // 18 x 10 halo per channel slice
+constexpr int U_HV = 3 * U_HY * U_HX;                       // 540 voxels
+constexpr int U_CHUNK = U_HV * 16;                          // bytes of one 8-feature chunk plane: 8640
+constexpr int U_HALO = 4 * U_CHUNK;                         // 34560
+constexpr int U_W = NTAP * 4 * C * 16;                      // 55296
+constexpr int conv05_smem = U_HALO + U_W + 64;              // + mbarrier and TMEM address slot
+constexpr uint32_t kIdescBf16 = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(C >> 3) << 17) |
+                                ((uint32_t)(128 >> 4) << 24);   // D f32, A/B bf16, K-major, N = 32, M = 128
+constexpr long long kWaitLimit = 1LL << 20;   // polls; each may suspend for a bounded time
+
+__device__ int g_tc_timeouts;
+
+__device__ __forceinline__ uint64_t umma_desc(uint32_t addr, uint32_t lbo, uint32_t sbo) {
+  uint64_t d = (uint64_t)((addr >> 4) & 0x3FFFu);
+  d |= (uint64_t)((lbo >> 4) & 0x3FFFu) << 16;
+  d |= (uint64_t)((sbo >> 4) & 0x3FFFu) << 32;
+  d |= (uint64_t)1 << 46;   // descriptor version of sm_100 and later; swizzle mode 0 (none)
+  return d;
+}
+
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+
 template <int EPI>
-__global__ void __launch_bounds__(256, 2)
-k_conv_tc(const bf16* __restrict__ in, const bf16* __restrict__ wk, const float* __restrict__ bias,
-          const bf16* __restrict__ mask, bf16* __restrict__ out, Dims d) {
+__global__ void __launch_bounds__(128)
+k_conv_tc05(const bf16* __restrict__ in, const bf16* __restrict__ wk, const float* __restrict__ bias,
+            const bf16* __restrict__ mask, bf16* __restrict__ out, Dims d, int tiles_x, int tiles_y, int ntiles) {
   extern __shared__ __align__(128) unsigned char smem[];
-  const uint32_t s_w = smem_u32(smem);
-  const uint32_t s_a = s_w + NTAP * C * ROWB;
-  for (int i = threadIdx.x; i < NTAP * C * 4; i += blockDim.x) {
-    const int rr = i >> 2, c = i & 3;
-    cp_async16(s_w + swz(rr, c), wk + rr * C + c * 8, 16);
-  }
+  const uint32_t s_halo = smem_u32(smem);
+  const uint32_t s_w = s_halo + U_HALO;
+  const uint32_t s_bar = s_w + U_W;            // mbarrier (8 B)
+  const uint32_t s_tm = s_bar + 8;             // TMEM address written by tcgen05.alloc
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int g = lane >> 2, tq = lane & 3;
-  const int a_vox = (lane & 7) + ((lane >> 3) & 1) * 8;   // ldmatrix row of the A strip
-  const int a_chk = lane >> 4;
-  const int b_row = (lane & 7) + ((lane >> 4) << 3);      // weight row within a pair of n-tiles
-  const int b_chk = (lane >> 3) & 1;
-  float bn[4][2];
-#pragma unroll
-  for (int nt = 0; nt < 4; ++nt) {
-    const int n = nt * 8 + tq * 2;
-    bn[nt][0] = (EPI != EPI_MASK && bias) ? bias[n] : 0.f;
-    bn[nt][1] = (EPI != EPI_MASK && bias) ? bias[n + 1] : 0.f;
-  }
 
-  for (int tile = blockIdx.x; tile < d.ntiles; tile += gridDim.x) {
-    int z0, y0, x0;
-    tile_origin(tile, d, z0, y0, x0);
-    __syncthreads();                       // the previous tile's reads are done
-    load_map_halo<HZ>(s_a, in, d, z0 - 1, y0, x0);
+  // weights [tap][co][ci] -> [tap][chunk][co][16 B]
+  for (int i = threadIdx.x; i < NTAP * C * 4; i += blockDim.x) {
+    const int c = i & 3, co = (i >> 2) & 31, t = i >> 7;
+    cp_async16(s_w + (uint32_t)(((t * 4 + c) * C + co) * 16), wk + (t * C + co) * C + c * 8, 16);
+  }
+  if (threadIdx.x == 0) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(s_bar) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 32;" ::"r"(s_tm) : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  uint32_t tmem;
+  asm volatile("ld.shared.b32 %0, [%1];" : "=r"(tmem) : "r"(s_tm) : "memory");
+
+  float bn[C];
+#pragma unroll
+  for (int c = 0; c < C; ++c) bn[c] = (EPI != EPI_MASK && bias) ? bias[c] : 0.f;
+
+  uint32_t phase = 0;
+  bool ok = true;
+  for (int tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x) {
+    const int txi = tile % tiles_x, rr = tile / tiles_x;
+    const int x0 = txi * U_TX, y0 = (rr % tiles_y) * U_TY, z0 = rr / tiles_y;
+    // halo: channels z0-1 .. z0+1, rows y0-1 .. y0+16, columns x0-1 .. x0+8, zero outside the cube
+    for (int i = threadIdx.x; i < U_HV * 4; i += blockDim.x) {
+      const int c = i & 3, h = i >> 2;
+      const int hx = h % U_HX, q = h / U_HX, hy = q % U_HY, hz = q / U_HY;
+      const int gz = z0 - 1 + hz, gy = y0 - 1 + hy, gx = x0 - 1 + hx;
+      const bool inb = inside(d, gz, gy, gx);
+      const bf16* src = inb ? in + vox(d, gz, gy, gx) * C + c * 8 : in;
+      cp_async16(s_halo + (uint32_t)(c * U_CHUNK + h * 16), src, inb ? 16 : 0);
+    }
     cp_async_wait_all();
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");   // smem written by this proxy, read by the MMA
+    tc_fence_before();
     __syncthreads();
-
-    float acc[2][4][4];
-#pragma unroll
-    for (int r = 0; r < 2; ++r)
-#pragma unroll
-      for (int nt = 0; nt < 4; ++nt)
-#pragma unroll
-        for (int e = 0; e < 4; ++e) acc[r][nt][e] = 0.f;
-
-    const int row0 = warp * 2;
+    tc_fence_after();
+    if (threadIdx.x == 0) {
 #pragma unroll 1
-    for (int t = 0; t < NTAP; ++t) {
-      const int kz = t / 9, ky = (t / 3) % 3, kx = t % 3;
+      for (int t = 0; t < NTAP; ++t) {
+        const int kz = t / 9, ky = (t / 3) % 3, kx = t % 3;
+        const uint32_t a0 = s_halo + (uint32_t)(((kz * U_HY + ky) * U_HX + kx) * 16);
+        const uint32_t b0 = s_w + (uint32_t)(t * 4 * C * 16);
 #pragma unroll
-      for (int kc = 0; kc < 2; ++kc) {
-        uint32_t b[4][2];
-#pragma unroll
-        for (int p = 0; p < 2; ++p)
-          ldsm_x4(s_w + swz(t * C + p * 16 + b_row, kc * 2 + b_chk), b[2 * p][0], b[2 * p][1], b[2 * p + 1][0],
-                  b[2 * p + 1][1]);
-#pragma unroll
-        for (int r = 0; r < 2; ++r) {
-          const int row = row0 + r, tz = row >> 3, ty = row & 7;
-          const int h = ((tz + kz) * HY + ty + ky) * HX + kx + a_vox;
-          uint32_t a[4];
-          ldsm_x4(s_a + swz(h, kc * 2 + a_chk), a[0], a[1], a[2], a[3]);
-#pragma unroll
-          for (int nt = 0; nt < 4; ++nt) mma_bf16(acc[r][nt], a, b[nt][0], b[nt][1]);
+        for (int kk = 0; kk < 2; ++kk) {
+          const uint64_t ad = umma_desc(a0 + kk * 2 * U_CHUNK, U_CHUNK, U_HX * 16);
+          const uint64_t bd = umma_desc(b0 + kk * 2 * C * 16, C * 16, 8 * 16);
+          const uint32_t acc = (t | kk) != 0;
+          asm volatile(
+              "{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
+              "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem),
+              "l"(ad), "l"(bd), "r"(kIdescBf16), "r"(acc)
+              : "memory");
         }
       }
+      asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(s_bar)
+                   : "memory");
     }
-
+    // wait for the MMAs (bounded)
+    uint32_t done = 0;
+    for (long long it = 0; it < kWaitLimit && !done; ++it) {
+      asm volatile(
+          "{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\nselp.u32 %0, 1, 0, p;\n}\n"
+          : "=r"(done)
+          : "r"(s_bar), "r"(phase)
+          : "memory");
+    }
+    if (__syncthreads_or(!done)) {          // one decision for the whole block
+      if (threadIdx.x == 0) atomicAdd(&g_tc_timeouts, 1);
+      ok = false;
+      break;
+    }
+    phase ^= 1u;
+    tc_fence_after();
+    uint32_t r[C];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+        "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];\n"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
+          "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
+          "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+        : "r"(tmem + ((uint32_t)(warp * 32) << 16)));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+    // row m = 32 warp + lane of D is output voxel (y0 + m / 8, x0 + m % 8) of channel z0
+    const int m = warp * 32 + lane;
+    const int z = z0, y = y0 + (m >> 3), x = x0 + (m & 7);
+    if (inside(d, z, y, x)) {
+      const size_t base = vox(d, z, y, x) * C;
+      float v[C];
 #pragma unroll
-    for (int r = 0; r < 2; ++r) {
-      const int row = row0 + r;
-      const int z = z0 + (row >> 3), y = y0 + (row & 7);
+      for (int c = 0; c < C; ++c) v[c] = __uint_as_float(r[c]);
+      if (EPI == EPI_MASK) {
+        if (mask) {
+          const uint4* mp = reinterpret_cast<const uint4*>(mask + base);
 #pragma unroll
-      for (int hf = 0; hf < 2; ++hf) {
-        const int x = x0 + g + hf * 8;
-        if (!inside(d, z, y, x)) continue;
-        const size_t base = vox(d, z, y, x) * C;
+          for (int q = 0; q < 4; ++q) {
+            float mf[8];
+            unpack8(mp[q], mf);
 #pragma unroll
-        for (int nt = 0; nt < 4; ++nt) {
-          const int n = nt * 8 + tq * 2;
-          float v0 = acc[r][nt][hf * 2], v1 = acc[r][nt][hf * 2 + 1];
-          if (EPI == EPI_MASK) {
-            if (mask) {
-              const float2 m = __bfloat1622float2(*reinterpret_cast<const bf162*>(mask + base + n));
-              if (!(m.x > 0.f)) v0 = 0.f;
-              if (!(m.y > 0.f)) v1 = 0.f;
-            }
-          } else {
-            v0 += bn[nt][0];
-            v1 += bn[nt][1];
-            if (EPI == EPI_RELU) {
-              v0 = fmaxf(v0, 0.f);
-              v1 = fmaxf(v1, 0.f);
-            }
+            for (int e = 0; e < 8; ++e)
+              if (!(mf[e] > 0.f)) v[8 * q + e] = 0.f;
           }
-          *reinterpret_cast<bf162*>(out + base + n) = __floats2bfloat162_rn(v0, v1);
+        }
+      } else {
+#pragma unroll
+        for (int c = 0; c < C; ++c) {
+          v[c] += bn[c];
+          if (EPI == EPI_RELU) v[c] = fmaxf(v[c], 0.f);
         }
       }
+      uint4* o = reinterpret_cast<uint4*>(out + base);
+#pragma unroll
+      for (int q = 0; q < 4; ++q) o[q] = pack8(v + 8 * q);
     }
+    tc_fence_before();
+    __syncthreads();     // TMEM read and halo consumed before the next tile overwrites them
+    tc_fence_after();
   }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 32;" ::"r"(tmem) : "memory");
 }
 
 // Weight (and bias) gradient of a 32 -> 32 layer: part[b][tap][co][ci] =
@@ -860,9 +933,9 @@ cudaError_t configure_once(int K) {
   static cudaError_t last_err[kMaxOut + 1] = {};
   if (!mid_done) {
     mid_done = true;
-    if ((mid_err = muffin::allow_max_dyn_smem(k_conv_tc<EPI_RELU>)) == cudaSuccess &&
-        (mid_err = muffin::allow_max_dyn_smem(k_conv_tc<EPI_BIAS>)) == cudaSuccess)
-      mid_err = muffin::allow_max_dyn_smem(k_conv_tc<EPI_MASK>);
+    if ((mid_err = muffin::allow_max_dyn_smem(k_conv_tc05<EPI_RELU>)) == cudaSuccess &&
+        (mid_err = muffin::allow_max_dyn_smem(k_conv_tc05<EPI_BIAS>)) == cudaSuccess)
+      mid_err = muffin::allow_max_dyn_smem(k_conv_tc05<EPI_MASK>);
   }
   if (mid_err != cudaSuccess) return mid_err;
   if (K < 1 || K > kMaxOut) return cudaSuccess;
@@ -876,10 +949,15 @@ cudaError_t configure_once(int K) {
 // Launch helpers (all persistent: grids bounded by the tile count).
 void launch_conv(int epi, const bf16* in, const bf16* wk, const float* bias, const bf16* mask, bf16* out,
                  const Dims& d, int sms, cudaStream_t st) {
-  const int grid = d.ntiles < 2 * sms ? d.ntiles : 2 * sms;
-  if (epi == EPI_RELU) k_conv_tc<EPI_RELU><<<grid, 256, conv_smem, st>>>(in, wk, bias, mask, out, d);
-  else if (epi == EPI_BIAS) k_conv_tc<EPI_BIAS><<<grid, 256, conv_smem, st>>>(in, wk, bias, mask, out, d);
-  else k_conv_tc<EPI_MASK><<<grid, 256, conv_smem, st>>>(in, wk, bias, mask, out, d);
+  const int tx = (d.nx + U_TX - 1) / U_TX, ty = (d.ny + U_TY - 1) / U_TY;
+  const int ntiles = tx * ty * d.nz;
+  const int grid = ntiles < 2 * sms ? ntiles : 2 * sms;
+  if (epi == EPI_RELU)
+    k_conv_tc05<EPI_RELU><<<grid, 128, conv05_smem, st>>>(in, wk, bias, mask, out, d, tx, ty, ntiles);
+  else if (epi == EPI_BIAS)
+    k_conv_tc05<EPI_BIAS><<<grid, 128, conv05_smem, st>>>(in, wk, bias, mask, out, d, tx, ty, ntiles);
+  else
+    k_conv_tc05<EPI_MASK><<<grid, 128, conv05_smem, st>>>(in, wk, bias, mask, out, d, tx, ty, ntiles);
 }
 
 void launch_wgrad_mid(const bf16* a, const bf16* dz, float* part, float* bpart, float* dw, float* db, const Dims& d,
@@ -1178,6 +1256,13 @@ int muffin_net_train_step(muffin_net* n, const float* d_dirty, const float* d_tx
   k_adam<<<(np + 255) / 256, 256, 0, n->st>>>(n->theta, n->grad, n->mom1, n->mom2, np, lr, (float)c1, (float)c2);
   unpack_params(n);
   return cuda_check(n, "muffin_net_train_step");
+}
+
+int muffin_net_wait_timeouts(void) {
+  int v = 0, zero = 0;
+  if (cudaMemcpyFromSymbol(&v, g_tc_timeouts, sizeof(int)) != cudaSuccess) return -1;
+  if (cudaMemcpyToSymbol(g_tc_timeouts, &zero, sizeof(int)) != cudaSuccess) return -1;
+  return v;
 }
 
 const char* muffin_net_last_error(const muffin_net* n) {

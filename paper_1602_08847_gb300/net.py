@@ -26,6 +26,7 @@ _SIG = {
     "muffin_net_loss_grad": (_I, [_P, _P, _P, _P, _P, ctypes.POINTER(ctypes.c_double)]),
     "muffin_net_train_step": (_I, [_P, _P, _P, _P, _F, _P]),
     "muffin_net_last_error": (ctypes.c_char_p, [_P]),
+    "muffin_net_wait_timeouts": (_I, []),
     "muffin_net_destroy": (None, [_P]),
     "muffin_conv3d_scratch_bytes": (_S, [_I, _I, _I]),
     "muffin_conv3d_forward": (_I, [_P, _P, _P, _I, _P, _I, _I, _I, _P, _S, _P]),
@@ -50,6 +51,11 @@ def n_params(n_out: int = 1) -> int:
 
 
 N_PARAMS = n_params(1)
+
+
+def wait_timeouts() -> int:
+    """Tensor-core waits that gave up since the last call (0 in a healthy run)."""
+    return int(_lib.muffin_net_wait_timeouts())
 
 
 def _ptr(t):

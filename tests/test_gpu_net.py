@@ -251,3 +251,8 @@ def test_network_argument_errors(netmod):
         m.loss_grad(torch.zeros((2, 8, 8), device="cuda"), torch.zeros((2, 8, 8), device="cuda"))
     with pytest.raises(Exception):
         n.loss_grad(torch.zeros((2, 8, 8), device="cuda"), torch.zeros((2, 8, 8), device="cuda"))
+
+
+def test_no_tensor_core_wait_gave_up(netmod):
+    """Every bounded wait of the tcgen05 layers above ended by completion."""
+    assert netmod.wait_timeouts() == 0
