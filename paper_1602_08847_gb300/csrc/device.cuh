@@ -85,14 +85,22 @@ __device__ __forceinline__ cpx<T> twiddle(const cpx<T>* tw, int idx) {
   return DIR < 0 ? w : conj(w);
 }
 
+// Shared-memory slot of element i with PAD: one spare slot after every 8
+// elements.  The first radix-8 pass writes 8 consecutive elements per thread,
+// so neighbouring threads' writes are 8 elements apart; the spare slot moves
+// them onto different banks, and runs of consecutive elements stay
+// consecutive within each group of 8.
+template <int PAD> __host__ __device__ __forceinline__ constexpr int fft_slot(int i) { return PAD ? i + (i >> 3) : i; }
+template <int N, int PAD> __host__ __device__ constexpr int fft_slots() { return PAD ? N + N / 8 : N; }
+
 // Length-N FFT (unnormalised, sign DIR) by the Stockham auto-sort scheme of
 // Govindaraju et al. (SC'08), one thread per 8 elements.
 // On entry thread t (0 <= t < N/8) holds v[q] = x[t + q N/8]; on exit it holds
 // X[t + q N/8] in natural order.  Intermediate passes go through sm, where
-// element i of this transform lives at sm[i * IS].  tw[m] = exp(-2 pi i m / N).
-// Every thread of the block must call this the same number of times (it
-// synchronises the whole block).
-template <typename T, int N, int DIR, int IS>
+// element i of this transform lives at sm[fft_slot<PAD>(i) * IS].
+// tw[m] = exp(-2 pi i m / N).  Every thread of the block must call this the
+// same number of times (it synchronises the whole block).
+template <typename T, int N, int DIR, int IS, int PAD = 0>
 __device__ __forceinline__ void fft_regs(cpx<T> (&v)[8], cpx<T>* sm, const cpx<T>* tw, int t) {
   using PL = FftPlan<N>;
   constexpr int T8 = PL::T8;
@@ -103,7 +111,7 @@ __device__ __forceinline__ void fft_regs(cpx<T> (&v)[8], cpx<T>* sm, const cpx<T
     if (p > 0) {
       __syncthreads();
 #pragma unroll
-      for (int q = 0; q < 8; ++q) v[q] = sm[(t + q * T8) * IS];
+      for (int q = 0; q < 8; ++q) v[q] = sm[fft_slot<PAD>(t + q * T8) * IS];
     }
     if (p < PL::P8) {
       const int k = t % Ns;
@@ -115,7 +123,7 @@ __device__ __forceinline__ void fft_regs(cpx<T> (&v)[8], cpx<T>* sm, const cpx<T
         __syncthreads();
         const int base = (t - k) * 8 + k;
 #pragma unroll
-        for (int r = 0; r < 8; ++r) sm[(base + r * Ns) * IS] = v[r];
+        for (int r = 0; r < 8; ++r) sm[fft_slot<PAD>(base + r * Ns) * IS] = v[r];
       }
       Ns *= 8;
     } else {
@@ -134,8 +142,8 @@ __device__ __forceinline__ void fft_regs(cpx<T> (&v)[8], cpx<T>* sm, const cpx<T
         const int b0 = (j0 - k0) * 4 + k0, b1 = (j1 - k1) * 4 + k1;
 #pragma unroll
         for (int r = 0; r < 4; ++r) {
-          sm[(b0 + r * Ns) * IS] = v[2 * r];
-          sm[(b1 + r * Ns) * IS] = v[2 * r + 1];
+          sm[fft_slot<PAD>(b0 + r * Ns) * IS] = v[2 * r];
+          sm[fft_slot<PAD>(b1 + r * Ns) * IS] = v[2 * r + 1];
         }
       }
       Ns *= 4;

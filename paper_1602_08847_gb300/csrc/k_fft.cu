@@ -25,9 +25,9 @@ template <int N> __host__ __device__ constexpr int cols_per_cta() { return N >= 
 template <int N>
 __global__ void __launch_bounds__(rows_pairs<N>() * (N / 8))
 k_rows_fwd(const float* __restrict__ X, cpx<float>* __restrict__ spec, const cpx<float>* __restrict__ twg) {
-  constexpr int T8 = N / 8, PAIRS = rows_pairs<N>(), H = N / 2;
+  constexpr int T8 = N / 8, PAIRS = rows_pairs<N>(), H = N / 2, NP = fft_slots<N, 1>();
   __shared__ cpx<float> tw[N];
-  __shared__ cpx<float> buf[PAIRS * N];
+  __shared__ cpx<float> buf[PAIRS * NP];
   const int f = threadIdx.x / T8, t = threadIdx.x % T8;
   for (int i = threadIdx.x; i < N; i += blockDim.x) tw[i] = twg[i];
   const int l = blockIdx.y;
@@ -37,23 +37,23 @@ k_rows_fwd(const float* __restrict__ X, cpx<float>* __restrict__ spec, const cpx
 #pragma unroll
   for (int q = 0; q < 8; ++q) v[q] = mk<float>(__ldg(r0 + t + q * T8), __ldg(r0 + N + t + q * T8));
   __syncthreads();
-  fft_regs<float, N, -1, 1>(v, buf + f * N, tw, t);
+  fft_regs<float, N, -1, 1, 1>(v, buf + f * NP, tw, t);
   __syncthreads();
 #pragma unroll
-  for (int q = 0; q < 8; ++q) buf[f * N + t + q * T8] = v[q];
+  for (int q = 0; q < 8; ++q) buf[f * NP + fft_slot<1>(t + q * T8)] = v[q];
   __syncthreads();
   cpx<float>* o0 = spec + ((size_t)l * N + y0) * H;
   cpx<float>* o1 = o0 + H;
 #pragma unroll
   for (int q = 0; q < 4; ++q) {
     const int k = t + q * T8;
-    const cpx<float> zk = buf[f * N + k];
+    const cpx<float> zk = buf[f * NP + fft_slot<1>(k)];
     if (k == 0) {
-      const cpx<float> zn = buf[f * N + H];
+      const cpx<float> zn = buf[f * NP + fft_slot<1>(H)];
       o0[0] = mk<float>(zk.x, zn.x);
       o1[0] = mk<float>(zk.y, zn.y);
     } else {
-      const cpx<float> zm = buf[f * N + N - k];
+      const cpx<float> zm = buf[f * NP + fft_slot<1>(N - k)];
       o0[k] = mk<float>(0.5f * (zk.x + zm.x), 0.5f * (zk.y - zm.y));
       o1[k] = mk<float>(0.5f * (zk.y + zm.y), 0.5f * (zm.x - zk.x));
     }
@@ -110,9 +110,9 @@ template <int N, int MODE>
 __global__ void __launch_bounds__(rows_pairs<N>() * (N / 8), 2)
 k_rows_inv(const cpx<float>* __restrict__ spec, PrimalArgs a, float* __restrict__ out,
            const cpx<float>* __restrict__ twg) {
-  constexpr int T8 = N / 8, PAIRS = rows_pairs<N>(), H = N / 2;
+  constexpr int T8 = N / 8, PAIRS = rows_pairs<N>(), H = N / 2, NP = fft_slots<N, 1>();
   __shared__ cpx<float> tw[N];
-  __shared__ cpx<float> buf[PAIRS * N];
+  __shared__ cpx<float> buf[PAIRS * NP];
   const int f = threadIdx.x / T8, t = threadIdx.x % T8;
   for (int i = threadIdx.x; i < N; i += blockDim.x) tw[i] = twg[i];
   const int l = blockIdx.y;
@@ -156,7 +156,7 @@ k_rows_inv(const cpx<float>* __restrict__ spec, PrimalArgs a, float* __restrict_
     }
   }
   __syncthreads();
-  fft_regs<float, N, 1, 1>(v, buf + f * N, tw, t);
+  fft_regs<float, N, 1, 1, 1>(v, buf + f * NP, tw, t);
 #pragma unroll
   for (int q = 0; q < 8; ++q) {
     const int x = t + q * T8;

@@ -63,6 +63,27 @@ __device__ __forceinline__ void win(const float* __restrict__ src, int stride, f
   }
 }
 
+// Same on the difference src - sub (both read at the same offsets).
+template <int D>
+__device__ __forceinline__ void win_diff(const float* __restrict__ src, const float* __restrict__ sub, int stride,
+                                         float (&out)[kQ]) {
+  if constexpr (D <= 4) {
+    float w[kQ + 4 * D];
+#pragma unroll
+    for (int t = 0; t < kQ + 4 * D; ++t) w[t] = src[(t - 2 * D) * stride] - sub[(t - 2 * D) * stride];
+#pragma unroll
+    for (int i = 0; i < kQ; ++i) out[i] = b3(w[i], w[i + D], w[i + 2 * D], w[i + 3 * D], w[i + 4 * D]);
+  } else {
+#pragma unroll
+    for (int i = 0; i < kQ; ++i) {
+      const float* p = src + i * stride;
+      const float* q = sub + i * stride;
+      out[i] = b3(p[-2 * D * stride] - q[-2 * D * stride], p[-D * stride] - q[-D * stride], p[0] - q[0],
+                  p[D * stride] - q[D * stride], p[2 * D * stride] - q[2 * D * stride]);
+    }
+  }
+}
+
 // Same along a periodic axis of length mm + 1: element t at base[((c0 + t) & mm) * stride].
 template <int D>
 __device__ __forceinline__ void win_per(const float* __restrict__ base, int stride, int c0, int mm, float (&out)[kQ]) {
@@ -129,6 +150,22 @@ __device__ __forceinline__ void fine_pass1(const float* __restrict__ X, float* _
     const int r0 = r0o + kQ <= rend ? r0o : rend - kQ;
     float o[kQ];
     win<D>(X + r0 * PA + c, PA, o);
+#pragma unroll
+    for (int i = 0; i < kQ; ++i)
+      if (r0 + i >= r0o) T[c * PT + r0 + i] = o[i];
+  }
+}
+
+// pass 1 on the difference X - Y (gen-1 adjoint: H_j (r - u_j) without storing r - u_j)
+template <int HM, int PA, int PT, int D>
+__device__ __forceinline__ void fine_pass1_diff(const float* __restrict__ X, const float* __restrict__ Y,
+                                                float* __restrict__ T, int ei, int eo) {
+  const int ncol = kTile + 2 * ei, nseg = (kTile + 2 * eo + kQ - 1) / kQ, rend = HM + kTile + eo;
+  for (int it = threadIdx.x; it < ncol * nseg; it += blockDim.x) {
+    const int c = HM - ei + it % ncol, r0o = HM - eo + (it / ncol) * kQ;
+    const int r0 = r0o + kQ <= rend ? r0o : rend - kQ;
+    float o[kQ];
+    win_diff<D>(X + r0 * PA + c, Y + r0 * PA + c, PA, o);
 #pragma unroll
     for (int i = 0; i < kQ; ++i)
       if (r0 + i >= r0o) T[c * PT + r0 + i] = o[i];
@@ -317,19 +354,14 @@ __device__ __forceinline__ void fine_adjoint_level(float*& R, float*& Ub, float*
     }
   }
   if constexpr (GEN == 1) {
-    constexpr int side = kTile + 2 * er;
-    region_for<side>([&](int r, int c) {
-      const int i = (HM - er + r) * PA + HM - er + c;
-      R[i] -= Ub[i];
-    });
-    __syncthreads();
+    fine_pass1_diff<HM, PA, PT, D>(R, Ub, T, er, en);     // H_j (r - u_j), first pass
   } else {
     fine_pass1<HM, PA, PT, D>(Ub, T, eu, er);
     __syncthreads();
     fine_pass2<HM, PT, D>(T, er, er, [&](int r, int c, float v) { R[r * PA + c] -= v; });
     __syncthreads();
+    fine_pass1<HM, PA, PT, D>(R, T, er, en);
   }
-  fine_pass1<HM, PA, PT, D>(R, T, er, en);
   __syncthreads();
   fine_pass2<HM, PT, D>(T, en, en, [&](int r, int c, float v) { Ub[r * PA + c] += v; });
   __syncthreads();
