@@ -12,7 +12,10 @@
 //   g[t] = (-1)^t h[2p-1-t];
 // its adjoint (= inverse, the bank is orthonormal):
 //   x[i] = sum_{t = i mod 2} h[t] lo[k] + g[t] hi[k],  k = ((i - t) mod M) / 2.
-// Every launch covers all channels and all eight bases (gridDim.z = 8 L).
+// Every launch covers all channels and all eight bases (gridDim.z = 8 L);
+// each thread computes a run of outputs (kRowsPerBlock rows per block in the
+// row kernels, kColRun outputs per thread in the column kernels), so blocks
+// live long enough to amortise their scheduling.
 // The levels are short (at most a few MB per basis and channel) and the filters
 // at most 16 taps: the kernels read straight from global memory through L1.
 #include <cuda_runtime.h>
@@ -123,49 +126,74 @@ cudaError_t dwt_configure() {
 // ------------------------------------------------------------------ kernels
 
 constexpr float kUnionScale = 0.35355339059327373f;   // 1/sqrt(8)
+constexpr int kRowsPerBlock = 8;
+constexpr int kColRun = 4;
+
+// The kernels below run one body per basis, instantiated for its filter length
+// (TAPS = 2p, compile time) so that every tap loop unrolls and its loads issue
+// together; the block's basis b = blockIdx.z & 7 picks the body.
+#define MUFFIN_DB_DISPATCH(CALL) \
+  switch (blockIdx.z & 7) {      \
+    case 0: CALL(2); break;      \
+    case 1: CALL(4); break;      \
+    case 2: CALL(6); break;      \
+    case 3: CALL(8); break;      \
+    case 4: CALL(10); break;     \
+    case 5: CALL(12); break;     \
+    case 6: CALL(14); break;     \
+    default: CALL(16); break;    \
+  }
 
 // Analysis, rows of level M: W1[z][r][k] = lo, W1[z][r][M/2 + k] = hi, for
 // the level input (level 0: the shared input cube; else W2[z], the previous
-// level's low-low quadrant).  grid (x: output chunks, y: rows, z: 8 L).
+// level's low-low quadrant).  grid (1, row groups, 8 L).
+template <int TAPS>
+__device__ __forceinline__ void dwt_rows_body(const float* __restrict__ src0, const float* __restrict__ W2,
+                                              float* __restrict__ W1, int n, int M, int level0) {
+  const int z = blockIdx.z, b = z & 7, l = z >> 3;
+  const int H = M >> 1, m = M - 1;
+  const size_t P = (size_t)n * n;
+  const int r1 = min(M, (int)(blockIdx.y + 1) * kRowsPerBlock);
+  for (int r = blockIdx.y * kRowsPerBlock; r < r1; ++r) {
+    const float* src = (level0 ? src0 + (size_t)l * P : W2 + (size_t)z * P) + (size_t)r * n;
+    float* dst = W1 + (size_t)z * P + (size_t)r * n;
+    for (int k = threadIdx.x; k < H; k += blockDim.x) {
+      float x[TAPS];
+#pragma unroll
+      for (int t = 0; t < TAPS; ++t) x[t] = __ldg(src + ((2 * k + t) & m));
+      float lo = 0.f, hi = 0.f;
+#pragma unroll
+      for (int t = 0; t < TAPS; ++t) {
+        lo = fmaf(c_dbh[b][t], x[t], lo);
+        hi = fmaf(c_dbg[b][t], x[t], hi);
+      }
+      dst[k] = lo;
+      dst[H + k] = hi;
+    }
+  }
+}
+
 __global__ void k_dwt_rows(const float* __restrict__ src0, const float* __restrict__ W2, float* __restrict__ W1,
                            int n, int M, int level0) {
-  const int z = blockIdx.z, b = z & 7, l = z >> 3, r = blockIdx.y;
-  const int H = M >> 1, m = M - 1, taps = 2 * (b + 1);
-  const size_t P = (size_t)n * n;
-  const float* src = (level0 ? src0 + (size_t)l * P : W2 + (size_t)z * P) + (size_t)r * n;
-  float* dst = W1 + (size_t)z * P + (size_t)r * n;
-  for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < H; k += gridDim.x * blockDim.x) {
-    float lo = 0.f, hi = 0.f;
-    for (int t = 0; t < taps; ++t) {
-      const float x = __ldg(src + ((2 * k + t) & m));
-      lo = fmaf(c_dbh[b][t], x, lo);
-      hi = fmaf(c_dbg[b][t], x, hi);
-    }
-    dst[k] = lo;
-    dst[H + k] = hi;
-  }
+#define CALL(T) dwt_rows_body<T>(src0, W2, W1, n, M, level0)
+  MUFFIN_DB_DISPATCH(CALL)
+#undef CALL
 }
 
 // Analysis, columns of level M: outputs (k, c) = lo and (M/2 + k, c) = hi of
 // column c of W1[z].  The low-low quadrant feeds the next level (W2[z]) unless
 // this is the last level; every final coefficient w (scaled by 1/sqrt 8)
 // updates U: MODE_UPDATE U <- rho sat(U + k w) + (1 - rho) U, MODE_LINEAR U = w.
-// block (32 columns, 8 outputs).
-template <int MODE>
-__global__ void k_dwt_cols(const float* __restrict__ W1, float* __restrict__ W2, float* __restrict__ U, int n,
-                           int M, int last, float kk, float rho) {
+// block (32 columns, 8 outputs), kColRun outputs per thread.
+template <int MODE, int TAPS>
+__device__ __forceinline__ void dwt_cols_body(const float* __restrict__ W1, float* __restrict__ W2,
+                                              float* __restrict__ U, int n, int M, int last, float kk, float rho) {
   const int z = blockIdx.z, b = z & 7;
-  const int c = blockIdx.x * blockDim.x + threadIdx.x, k = blockIdx.y * blockDim.y + threadIdx.y;
-  const int H = M >> 1, m = M - 1, taps = 2 * (b + 1);
-  if (c >= M || k >= H) return;
+  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+  const int H = M >> 1, m = M - 1;
+  if (c >= M) return;
   const size_t P = (size_t)n * n;
   const float* col = W1 + (size_t)z * P + c;
-  float lo = 0.f, hi = 0.f;
-  for (int t = 0; t < taps; ++t) {
-    const float x = __ldg(col + (size_t)((2 * k + t) & m) * n);
-    lo = fmaf(c_dbh[b][t], x, lo);
-    hi = fmaf(c_dbg[b][t], x, hi);
-  }
   float* Uz = U + (size_t)z * P;
   auto put = [&](int row, float w) {
     float* u = Uz + (size_t)row * n + c;
@@ -177,48 +205,109 @@ __global__ void k_dwt_cols(const float* __restrict__ W1, float* __restrict__ W2,
       *u = w;
     }
   };
-  if (c < H && !last) W2[(size_t)z * P + (size_t)k * n + c] = lo;
-  else put(k, lo);
-  put(H + k, hi);
+#pragma unroll 1
+  for (int j = 0; j < kColRun; ++j) {
+    const int k = (blockIdx.y * kColRun + j) * blockDim.y + threadIdx.y;
+    if (k >= H) break;
+    float x[TAPS];
+#pragma unroll
+    for (int t = 0; t < TAPS; ++t) x[t] = __ldg(col + (size_t)((2 * k + t) & m) * n);
+    float lo = 0.f, hi = 0.f;
+#pragma unroll
+    for (int t = 0; t < TAPS; ++t) {
+      lo = fmaf(c_dbh[b][t], x[t], lo);
+      hi = fmaf(c_dbg[b][t], x[t], hi);
+    }
+    if (c < H && !last) W2[(size_t)z * P + (size_t)k * n + c] = lo;
+    else put(k, lo);
+    put(H + k, hi);
+  }
+}
+
+template <int MODE>
+__global__ void k_dwt_cols(const float* __restrict__ W1, float* __restrict__ W2, float* __restrict__ U, int n,
+                           int M, int last, float kk, float rho) {
+#define CALL(T) dwt_cols_body<MODE, T>(W1, W2, U, n, M, last, kk, rho)
+  MUFFIN_DB_DISPATCH(CALL)
+#undef CALL
 }
 
 // Adjoint, columns of level M: W1[z][i][c] from the low half (rows < M/2:
 // the low-low quadrant from W2[z], or from U at the coarsest level, next to the
 // U quadrant for c >= M/2) and the high half (U rows >= M/2).
-__global__ void k_idwt_cols(const float* __restrict__ U, const float* __restrict__ W2, float* __restrict__ W1,
-                            int n, int M, int coarsest) {
+template <int TAPS>
+__device__ __forceinline__ void idwt_cols_body(const float* __restrict__ U, const float* __restrict__ W2,
+                                               float* __restrict__ W1, int n, int M, int coarsest) {
   const int z = blockIdx.z, b = z & 7;
-  const int c = blockIdx.x * blockDim.x + threadIdx.x, i = blockIdx.y * blockDim.y + threadIdx.y;
-  const int H = M >> 1, m = M - 1, taps = 2 * (b + 1);
-  if (c >= M || i >= M) return;
+  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+  const int H = M >> 1, m = M - 1;
+  if (c >= M) return;
   const size_t P = (size_t)n * n;
   const float* lo = ((c < H && !coarsest) ? W2 : U) + (size_t)z * P + c;
   const float* hi = U + (size_t)z * P + (size_t)H * n + c;
-  float acc = 0.f;
-  for (int t = i & 1; t < taps; t += 2) {
-    const size_t kk = (size_t)(((i - t) & m) >> 1) * n;
-    acc = fmaf(c_dbh[b][t], __ldg(lo + kk), acc);
-    acc = fmaf(c_dbg[b][t], __ldg(hi + kk), acc);
+#pragma unroll 1
+  for (int j = 0; j < kColRun; ++j) {
+    const int i = (blockIdx.y * kColRun + j) * blockDim.y + threadIdx.y;
+    if (i >= M) break;
+    const int par = i & 1;
+    float a[TAPS / 2], d[TAPS / 2];
+#pragma unroll
+    for (int s2 = 0; s2 < TAPS / 2; ++s2) {
+      const size_t kk = (size_t)(((i - par - 2 * s2) & m) >> 1) * n;
+      a[s2] = __ldg(lo + kk);
+      d[s2] = __ldg(hi + kk);
+    }
+    float acc = 0.f;
+#pragma unroll
+    for (int s2 = 0; s2 < TAPS / 2; ++s2) {
+      acc = fmaf(c_dbh[b][par + 2 * s2], a[s2], acc);
+      acc = fmaf(c_dbg[b][par + 2 * s2], d[s2], acc);
+    }
+    W1[(size_t)z * P + (size_t)i * n + c] = acc;
   }
-  W1[(size_t)z * P + (size_t)i * n + c] = acc;
+}
+
+__global__ void k_idwt_cols(const float* __restrict__ U, const float* __restrict__ W2, float* __restrict__ W1,
+                            int n, int M, int coarsest) {
+#define CALL(T) idwt_cols_body<T>(U, W2, W1, n, M, coarsest)
+  MUFFIN_DB_DISPATCH(CALL)
+#undef CALL
 }
 
 // Adjoint, rows of level M: out[z][r][i] from W1[z][r][k] (low) and W1[z][r][M/2 + k] (high).
-__global__ void k_idwt_rows(const float* __restrict__ W1, float* __restrict__ out, int n, int M) {
-  const int z = blockIdx.z, b = z & 7, r = blockIdx.y;
-  const int H = M >> 1, m = M - 1, taps = 2 * (b + 1);
+template <int TAPS>
+__device__ __forceinline__ void idwt_rows_body(const float* __restrict__ W1, float* __restrict__ out, int n, int M) {
+  const int z = blockIdx.z, b = z & 7;
+  const int H = M >> 1, m = M - 1;
   const size_t P = (size_t)n * n;
-  const float* src = W1 + (size_t)z * P + (size_t)r * n;
-  float* dst = out + (size_t)z * P + (size_t)r * n;
-  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < M; i += gridDim.x * blockDim.x) {
-    float acc = 0.f;
-    for (int t = i & 1; t < taps; t += 2) {
-      const int kk = ((i - t) & m) >> 1;
-      acc = fmaf(c_dbh[b][t], __ldg(src + kk), acc);
-      acc = fmaf(c_dbg[b][t], __ldg(src + H + kk), acc);
+  const int r1 = min(M, (int)(blockIdx.y + 1) * kRowsPerBlock);
+  for (int r = blockIdx.y * kRowsPerBlock; r < r1; ++r) {
+    const float* src = W1 + (size_t)z * P + (size_t)r * n;
+    float* dst = out + (size_t)z * P + (size_t)r * n;
+    for (int i = threadIdx.x; i < M; i += blockDim.x) {
+      const int par = i & 1;
+      float a[TAPS / 2], d[TAPS / 2];
+#pragma unroll
+      for (int s2 = 0; s2 < TAPS / 2; ++s2) {
+        const int kk = ((i - par - 2 * s2) & m) >> 1;
+        a[s2] = __ldg(src + kk);
+        d[s2] = __ldg(src + H + kk);
+      }
+      float acc = 0.f;
+#pragma unroll
+      for (int s2 = 0; s2 < TAPS / 2; ++s2) {
+        acc = fmaf(c_dbh[b][par + 2 * s2], a[s2], acc);
+        acc = fmaf(c_dbg[b][par + 2 * s2], d[s2], acc);
+      }
+      dst[i] = acc;
     }
-    dst[i] = acc;
   }
+}
+
+__global__ void k_idwt_rows(const float* __restrict__ W1, float* __restrict__ out, int n, int M) {
+#define CALL(T) idwt_rows_body<T>(W1, out, n, M)
+  MUFFIN_DB_DISPATCH(CALL)
+#undef CALL
 }
 
 // S[l][p] = (1/sqrt 8) sum_b W2[l][b][p], bases summed in order.
@@ -248,8 +337,8 @@ cudaError_t launch_dwt_analysis(const Geom& g, const DwtArgs& a, int mode, cudaS
   const int n = g.n, Z = kDbBases * g.L;
   for (int j = 0; j < g.J; ++j) {
     const int M = n >> j, H = M >> 1;
-    k_dwt_rows<<<dim3((H + 127) / 128, M, Z), 128, 0, s>>>(a.src, a.W2, a.W1, n, M, j == 0);
-    const dim3 grid((M + 31) / 32, (H + 7) / 8, Z), block(32, 8);
+    k_dwt_rows<<<dim3(1, (M + kRowsPerBlock - 1) / kRowsPerBlock, Z), 128, 0, s>>>(a.src, a.W2, a.W1, n, M, j == 0);
+    const dim3 grid((M + 31) / 32, (H + 8 * kColRun - 1) / (8 * kColRun), Z), block(32, 8);
     const int last = j == g.J - 1;
     if (mode == MODE_UPDATE) k_dwt_cols<MODE_UPDATE><<<grid, block, 0, s>>>(a.W1, a.W2, a.U, n, M, last, a.k, a.rho);
     else k_dwt_cols<MODE_LINEAR><<<grid, block, 0, s>>>(a.W1, a.W2, a.U, n, M, last, 1.f, 1.f);
@@ -261,8 +350,9 @@ cudaError_t launch_dwt_adjoint(const Geom& g, const DwtArgs& a, cudaStream_t s) 
   const int n = g.n, Z = kDbBases * g.L;
   for (int j = g.J - 1; j >= 0; --j) {
     const int M = n >> j;
-    k_idwt_cols<<<dim3((M + 31) / 32, (M + 7) / 8, Z), dim3(32, 8), 0, s>>>(a.U, a.W2, a.W1, n, M, j == g.J - 1);
-    k_idwt_rows<<<dim3((M + 127) / 128, M, Z), 128, 0, s>>>(a.W1, a.W2, n, M);
+    k_idwt_cols<<<dim3((M + 31) / 32, (M + 8 * kColRun - 1) / (8 * kColRun), Z), dim3(32, 8), 0, s>>>(
+        a.U, a.W2, a.W1, n, M, j == g.J - 1);
+    k_idwt_rows<<<dim3(1, (M + kRowsPerBlock - 1) / kRowsPerBlock, Z), 128, 0, s>>>(a.W1, a.W2, n, M);
   }
   const size_t P = (size_t)n * n, total = (size_t)g.L * P;
   const int blocks = (int)std::min<size_t>((total + 255) / 256, 4096);
