@@ -26,6 +26,7 @@
 // output; they run on the CUDA cores.  Every reduction over voxels is a
 // per-block partial sum followed by a fixed-order sum: results do not depend
 // on scheduling.
+#include <cuda.h>            // CUtensorMap (the encoder is reached through the runtime's driver entry point)
 #include <cuda_runtime.h>
 #include <cuda_bf16.h>
 #include <stdint.h>
@@ -182,35 +183,52 @@ __device__ __forceinline__ uint4 pack8(const float* f) {
 
 enum { EPI_RELU = 0, EPI_BIAS = 1, EPI_MASK = 2 };
 
-// ------------------------------------------------------------------ 32 -> 32 layers on tcgen05 (UMMA)
+// ------------------------------------------------------------------ 32 -> 32 layers on tcgen05 (UMMA), fed by TMA
 //
-// One CTA of 128 threads owns 128 output voxels at a time (one channel, 16
-// rows, 8 columns): D[128 voxels][32 features] accumulates in tensor memory
-// over 27 taps x 2 steps of K = 16 by tcgen05.mma (kind::f16, bfloat16 A and
-// B, float32 D, M = 128, N = 32), both operands read from shared memory
-// through matrix descriptors in the canonical K-major layout without swizzle:
-// 8-row x 16-byte core matrices.  The halo tile (3 x 18 x 10 voxels) is stored
-// feature-chunk major, so the 8 consecutive voxels of one output row are one
-// core matrix in every tap's shifted window: rows of a window are 16 B apart,
-// the next output row (next 8-row group) is one halo row (160 B) further, and
-// the next 8 input features are one chunk plane (8640 B) further.  Weights are
-// stored [tap][chunk][co][16 B]: next 8 outputs 128 B, next 8 inputs 512 B.
-// Thread 0 issues the 54 MMAs and commits them to an mbarrier; every warp then
-// reads its 32 TMEM lanes (tcgen05.ld 32x32b.x32) for the epilogue.  Waits on
-// the mbarrier are bounded: on timeout the CTA records it in g_tc_timeouts,
-// skips the rest of its tiles and still frees its tensor memory.
+// One CTA of 128 threads walks output tiles of 128 voxels (one channel, 16
+// rows, 8 columns).  For each tile D[128 voxels][32 features] accumulates in
+// tensor memory over 27 taps x 2 steps of K = 16 by tcgen05.mma (kind::f16,
+// bfloat16 A and B, float32 D, M = 128, N = 32); both operands are read from
+// shared memory through descriptors in the canonical K-major layout without
+// swizzle (8-row x 16-byte core matrices).
+//
+// The tile's input halo (3 x 18 x 10 voxels) arrives by TMA: one
+// cp.async.bulk.tensor per 8-feature chunk, from a 4-D tensor map over
+// (8 features, x, y, z) of the [z][y][x][32] map (strides 64 B, 64 nx B,
+// 64 nx ny B; base offset 16 B per chunk).  A box lands as one chunk plane
+// [z][y][x][16 B], so the 8 consecutive voxels of an output row are one core
+// matrix in every tap's shifted window: rows of a window are 16 B apart, the
+// next output row (next 8-row group) is one halo row (160 B) further, the next
+// 8 input features one chunk plane further (planes padded to 8704 B, TMA wants
+// 128-byte aligned destinations).  Outside the cube the copy fills zeros: the
+// zero padding of the layer.  Weights are [tap][chunk][co][16 B] (next 8
+// outputs 128 B, next 8 inputs 512 B), loaded once per CTA.
+//
+// One halo buffer (90 KB of shared memory in all, two CTAs per SM): thread 0
+// issues tile i's MMAs (commit -> mbarrier mdone); once they have read the
+// halo, it issues the TMA of tile i+1 (mbarrier full), which then runs under
+// tile i's epilogue, while the SM's other CTA keeps the tensor core busy.
+// Every wait is bounded: on timeout the CTA records it in g_tc_timeouts,
+// waits (bounded) for its copy in flight, skips its remaining tiles and still
+// frees its tensor memory.
 constexpr int U_TY = 16, U_TX = 8;                          // output tile: 16 rows x 8 columns, one channel
 constexpr int U_HY = U_TY + 2, U_HX = U_TX + 2;             // 18 x 10 halo per channel slice
 constexpr int U_HV = 3 * U_HY * U_HX;                       // 540 voxels
-constexpr int U_CHUNK = U_HV * 16;                          // bytes of one 8-feature chunk plane: 8640
-constexpr int U_HALO = 4 * U_CHUNK;                         // 34560
+constexpr int U_BOX = U_HV * 16;                            // bytes of one chunk box: 8640
+constexpr int U_CHUNK = 8704;                               // chunk plane stride (128-byte multiple)
+constexpr int U_HALO = 4 * U_CHUNK;                         // 34816
 constexpr int U_W = NTAP * 4 * C * 16;                      // 55296
-constexpr int conv05_smem = U_HALO + U_W + 64;              // + mbarrier and TMEM address slot
+constexpr int U_BAR = U_HALO + U_W;                         // 2 mbarriers, then the TMEM address slot
+constexpr int conv05_smem = U_BAR + 64 + 128;               // + alignment slack
 constexpr uint32_t kIdescBf16 = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(C >> 3) << 17) |
                                 ((uint32_t)(128 >> 4) << 24);   // D f32, A/B bf16, K-major, N = 32, M = 128
 constexpr long long kWaitLimit = 1LL << 20;   // polls; each may suspend for a bounded time
 
 __device__ int g_tc_timeouts;
+
+struct HaloMaps {
+  CUtensorMap m[4];   // one per 8-feature chunk
+};
 
 __device__ __forceinline__ uint64_t umma_desc(uint32_t addr, uint32_t lbo, uint32_t sbo) {
   uint64_t d = (uint64_t)((addr >> 4) & 0x3FFFu);
@@ -223,24 +241,54 @@ __device__ __forceinline__ uint64_t umma_desc(uint32_t addr, uint32_t lbo, uint3
 __device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
 __device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
 
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
+  uint32_t done = 0;
+  for (long long it = 0; it < kWaitLimit && !done; ++it) {
+    asm volatile(
+        "{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\nselp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(done)
+        : "r"(bar), "r"(parity)
+        : "memory");
+  }
+  return done != 0;
+}
+
+// Thread 0: the four chunk boxes of the tile at (x0, y0, z0) into halo buffer s_dst.
+__device__ __forceinline__ void issue_halo(const HaloMaps& maps, uint32_t s_dst, uint32_t bar, int x0, int y0,
+                                           int z0) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(4 * U_BOX) : "memory");
+#pragma unroll
+  for (int c = 0; c < 4; ++c)
+    asm volatile(
+        "cp.async.bulk.tensor.4d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4, %5}], "
+        "[%6];" ::"r"(s_dst + (uint32_t)(c * U_CHUNK)),
+        "l"(reinterpret_cast<uint64_t>(&maps.m[c])), "r"(0), "r"(x0 - 1), "r"(y0 - 1), "r"(z0 - 1), "r"(bar)
+        : "memory");
+}
+
 template <int EPI>
 __global__ void __launch_bounds__(128)
-k_conv_tc05(const bf16* __restrict__ in, const bf16* __restrict__ wk, const float* __restrict__ bias,
+k_conv_tc05(const __grid_constant__ HaloMaps maps, const bf16* __restrict__ wk, const float* __restrict__ bias,
             const bf16* __restrict__ mask, bf16* __restrict__ out, Dims d, int tiles_x, int tiles_y, int ntiles) {
   extern __shared__ __align__(128) unsigned char smem[];
-  const uint32_t s_halo = smem_u32(smem);
-  const uint32_t s_w = s_halo + U_HALO;
-  const uint32_t s_bar = s_w + U_W;            // mbarrier (8 B)
-  const uint32_t s_tm = s_bar + 8;             // TMEM address written by tcgen05.alloc
+  const uint32_t s0 = (smem_u32(smem) + 127u) & ~127u;
+  const uint32_t s_halo = s0;
+  const uint32_t s_w = s0 + U_HALO;
+  const uint32_t s_full = s0 + U_BAR;              // TMA landed
+  const uint32_t s_done = s_full + 8;              // MMAs finished
+  const uint32_t s_tm = s_full + 16;               // TMEM address written by tcgen05.alloc
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
 
-  // weights [tap][co][ci] -> [tap][chunk][co][16 B]
+  // weights [tap][co][ci] -> [tap][chunk][co][16 B], once per CTA
   for (int i = threadIdx.x; i < NTAP * C * 4; i += blockDim.x) {
     const int c = i & 3, co = (i >> 2) & 31, t = i >> 7;
     cp_async16(s_w + (uint32_t)(((t * 4 + c) * C + co) * 16), wk + (t * C + co) * C + c * 8, 16);
   }
+  cp_async_wait_all();
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");   // generic-proxy writes, read by the MMA
   if (threadIdx.x == 0) {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(s_bar) : "memory");
+#pragma unroll
+    for (int b = 0; b < 2; ++b) asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(s_full + 8 * b) : "memory");
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   if (warp == 0) {
@@ -257,61 +305,68 @@ k_conv_tc05(const bf16* __restrict__ in, const bf16* __restrict__ wk, const floa
 #pragma unroll
   for (int c = 0; c < C; ++c) bn[c] = (EPI != EPI_MASK && bias) ? bias[c] : 0.f;
 
-  uint32_t phase = 0;
-  bool ok = true;
-  for (int tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x) {
+  auto origin = [&](int tile, int& x0, int& y0, int& z0) {
     const int txi = tile % tiles_x, rr = tile / tiles_x;
-    const int x0 = txi * U_TX, y0 = (rr % tiles_y) * U_TY, z0 = rr / tiles_y;
-    // halo: channels z0-1 .. z0+1, rows y0-1 .. y0+16, columns x0-1 .. x0+8, zero outside the cube
-    for (int i = threadIdx.x; i < U_HV * 4; i += blockDim.x) {
-      const int c = i & 3, h = i >> 2;
-      const int hx = h % U_HX, q = h / U_HX, hy = q % U_HY, hz = q / U_HY;
-      const int gz = z0 - 1 + hz, gy = y0 - 1 + hy, gx = x0 - 1 + hx;
-      const bool inb = inside(d, gz, gy, gx);
-      const bf16* src = inb ? in + vox(d, gz, gy, gx) * C + c * 8 : in;
-      cp_async16(s_halo + (uint32_t)(c * U_CHUNK + h * 16), src, inb ? 16 : 0);
-    }
-    cp_async_wait_all();
-    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");   // smem written by this proxy, read by the MMA
-    tc_fence_before();
-    __syncthreads();
-    tc_fence_after();
+    x0 = txi * U_TX;
+    y0 = (rr % tiles_y) * U_TY;
+    z0 = rr / tiles_y;
+  };
+  // thread 0 tracks the halo copy it may have in flight, so that an early
+  // exit can wait for it before the CTA's shared memory goes away
+  bool pending = false;
+  uint32_t pend_ph = 0;
+  if (threadIdx.x == 0 && (int)blockIdx.x < ntiles) {
+    int x0, y0, z0;
+    origin(blockIdx.x, x0, y0, z0);
+    issue_halo(maps, s_halo, s_full, x0, y0, z0);
+    pending = true;
+  }
+
+  int it = 0;
+  for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x, ++it) {
+    const uint32_t ph = (uint32_t)it & 1u;
+    int x0, y0, z0;
+    origin(tile, x0, y0, z0);
     if (threadIdx.x == 0) {
+      if (mbar_wait(s_full, ph)) {
+        pending = false;
+        tc_fence_after();
+        const uint32_t hb = s_halo;
+        const uint32_t dt = tmem;
 #pragma unroll 1
-      for (int t = 0; t < NTAP; ++t) {
-        const int kz = t / 9, ky = (t / 3) % 3, kx = t % 3;
-        const uint32_t a0 = s_halo + (uint32_t)(((kz * U_HY + ky) * U_HX + kx) * 16);
-        const uint32_t b0 = s_w + (uint32_t)(t * 4 * C * 16);
+        for (int t = 0; t < NTAP; ++t) {
+          const int kz = t / 9, ky = (t / 3) % 3, kx = t % 3;
+          const uint32_t a0 = hb + (uint32_t)(((kz * U_HY + ky) * U_HX + kx) * 16);
+          const uint32_t b0 = s_w + (uint32_t)(t * 4 * C * 16);
 #pragma unroll
-        for (int kk = 0; kk < 2; ++kk) {
-          const uint64_t ad = umma_desc(a0 + kk * 2 * U_CHUNK, U_CHUNK, U_HX * 16);
-          const uint64_t bd = umma_desc(b0 + kk * 2 * C * 16, C * 16, 8 * 16);
-          const uint32_t acc = (t | kk) != 0;
-          asm volatile(
-              "{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
-              "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem),
-              "l"(ad), "l"(bd), "r"(kIdescBf16), "r"(acc)
-              : "memory");
+          for (int kk = 0; kk < 2; ++kk) {
+            const uint64_t ad = umma_desc(a0 + kk * 2 * U_CHUNK, U_CHUNK, U_HX * 16);
+            const uint64_t bd = umma_desc(b0 + kk * 2 * C * 16, C * 16, 8 * 16);
+            const uint32_t acc = (t | kk) != 0;
+            asm volatile(
+                "{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
+                "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(dt),
+                "l"(ad), "l"(bd), "r"(kIdescBf16), "r"(acc)
+                : "memory");
+          }
         }
+        asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(s_done)
+                     : "memory");
       }
-      asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(s_bar)
-                   : "memory");
     }
-    // wait for the MMAs (bounded)
-    uint32_t done = 0;
-    for (long long it = 0; it < kWaitLimit && !done; ++it) {
-      asm volatile(
-          "{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\nselp.u32 %0, 1, 0, p;\n}\n"
-          : "=r"(done)
-          : "r"(s_bar), "r"(phase)
-          : "memory");
-    }
+    const bool done = mbar_wait(s_done, ph);
     if (__syncthreads_or(!done)) {          // one decision for the whole block
       if (threadIdx.x == 0) atomicAdd(&g_tc_timeouts, 1);
-      ok = false;
       break;
     }
-    phase ^= 1u;
+    // the MMAs have read the halo: the next tile's copy runs under this epilogue
+    if (threadIdx.x == 0 && tile + (int)gridDim.x < ntiles) {
+      int nx0, ny0, nz0;
+      origin(tile + gridDim.x, nx0, ny0, nz0);
+      issue_halo(maps, s_halo, s_full, nx0, ny0, nz0);
+      pending = true;
+      pend_ph = (uint32_t)(it + 1) & 1u;
+    }
     tc_fence_after();
     uint32_t r[C];
     asm volatile(
@@ -355,9 +410,10 @@ k_conv_tc05(const bf16* __restrict__ in, const bf16* __restrict__ wk, const floa
       for (int q = 0; q < 4; ++q) o[q] = pack8(v + 8 * q);
     }
     tc_fence_before();
-    __syncthreads();     // TMEM read and halo consumed before the next tile overwrites them
+    __syncthreads();     // the accumulator is read before the next tile's MMAs overwrite it
     tc_fence_after();
   }
+  if (threadIdx.x == 0 && pending) mbar_wait(s_full, pend_ph);   // only after a timeout
   tc_fence_before();
   __syncthreads();
   tc_fence_after();
@@ -947,17 +1003,70 @@ cudaError_t configure_once(int K) {
 }
 
 // Launch helpers (all persistent: grids bounded by the tile count).
-void launch_conv(int epi, const bf16* in, const bf16* wk, const float* bias, const bf16* mask, bf16* out,
-                 const Dims& d, int sms, cudaStream_t st) {
+typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                  const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+EncodeTiledFn encode_tiled() {
+  static EncodeTiledFn fn = nullptr;
+  static bool tried = false;
+  if (!tried) {
+    tried = true;
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+            cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<EncodeTiledFn>(p);
+  }
+  return fn;
+}
+
+// The four 4-D tensor maps (8 features, x, y, z) of a [z][y][x][32] bfloat16 map, one per chunk.
+cudaError_t halo_maps(const bf16* in, const Dims& d, HaloMaps* maps) {
+  EncodeTiledFn enc = encode_tiled();
+  if (!enc) return cudaErrorNotSupported;
+  const cuuint64_t dims[4] = {8, (cuuint64_t)d.nx, (cuuint64_t)d.ny, (cuuint64_t)d.nz};
+  const cuuint64_t strides[3] = {(cuuint64_t)C * 2, (cuuint64_t)d.nx * C * 2, (cuuint64_t)d.ny * d.nx * C * 2};
+  const cuuint32_t box[4] = {8, U_HX, U_HY, 3};
+  const cuuint32_t estr[4] = {1, 1, 1, 1};
+  for (int c = 0; c < 4; ++c) {
+    const CUresult r = enc(&maps->m[c], CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4, (void*)(in + c * 8), dims, strides,
+                           box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                           CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) return cudaErrorInvalidValue;
+  }
+  return cudaSuccess;
+}
+
+// A host-side failure of a layer launch (a tensor map that could not be
+// encoded), reported by the next status check of the calling entry point.
+cudaError_t g_launch_err = cudaSuccess;
+
+cudaError_t take_launch_error() {
+  const cudaError_t e = g_launch_err;
+  g_launch_err = cudaSuccess;
+  return e != cudaSuccess ? e : cudaGetLastError();
+}
+
+cudaError_t launch_conv(int epi, const bf16* in, const bf16* wk, const float* bias, const bf16* mask, bf16* out,
+                        const Dims& d, int sms, cudaStream_t st) {
+  HaloMaps maps;
+  const cudaError_t e = halo_maps(in, d, &maps);
+  if (e != cudaSuccess) {
+    g_launch_err = e;
+    return e;
+  }
   const int tx = (d.nx + U_TX - 1) / U_TX, ty = (d.ny + U_TY - 1) / U_TY;
   const int ntiles = tx * ty * d.nz;
-  const int grid = ntiles < 2 * sms ? ntiles : 2 * sms;
+  const int grid = ntiles < 2 * sms ? ntiles : 2 * sms;   // two CTAs per SM (90 KB of shared memory each)
   if (epi == EPI_RELU)
-    k_conv_tc05<EPI_RELU><<<grid, 128, conv05_smem, st>>>(in, wk, bias, mask, out, d, tx, ty, ntiles);
+    k_conv_tc05<EPI_RELU><<<grid, 128, conv05_smem, st>>>(maps, wk, bias, mask, out, d, tx, ty, ntiles);
   else if (epi == EPI_BIAS)
-    k_conv_tc05<EPI_BIAS><<<grid, 128, conv05_smem, st>>>(in, wk, bias, mask, out, d, tx, ty, ntiles);
+    k_conv_tc05<EPI_BIAS><<<grid, 128, conv05_smem, st>>>(maps, wk, bias, mask, out, d, tx, ty, ntiles);
   else
-    k_conv_tc05<EPI_MASK><<<grid, 128, conv05_smem, st>>>(in, wk, bias, mask, out, d, tx, ty, ntiles);
+    k_conv_tc05<EPI_MASK><<<grid, 128, conv05_smem, st>>>(maps, wk, bias, mask, out, d, tx, ty, ntiles);
+  return cudaGetLastError();
 }
 
 void launch_wgrad_mid(const bf16* a, const bf16* dz, float* part, float* bpart, float* dw, float* db, const Dims& d,
@@ -1055,7 +1164,7 @@ int fail(muffin_net* n, int code, const std::string& msg) {
 }
 
 int cuda_check(muffin_net* n, const char* what) {
-  const cudaError_t e = cudaGetLastError();
+  const cudaError_t e = take_launch_error();
   if (e != cudaSuccess) return fail(n, MUFFIN_ERR_CUDA, std::string(what) + ": " + cudaGetErrorString(e));
   return MUFFIN_OK;
 }
@@ -1282,7 +1391,7 @@ static int conv_fail(int code, const std::string& msg) {
 }
 
 static int conv_cuda(const char* what) {
-  const cudaError_t e = cudaGetLastError();
+  const cudaError_t e = take_launch_error();
   if (e != cudaSuccess) return conv_fail(MUFFIN_ERR_CUDA, std::string(what) + ": " + cudaGetErrorString(e));
   return MUFFIN_OK;
 }
