@@ -310,15 +310,45 @@ __global__ void k_idwt_rows(const float* __restrict__ W1, float* __restrict__ ou
 #undef CALL
 }
 
-// S[l][p] = (1/sqrt 8) sum_b W2[l][b][p], bases summed in order.
-__global__ void k_union_sum(const float* __restrict__ W2, float* __restrict__ S, size_t P, size_t total) {
-  for (size_t q = blockIdx.x * (size_t)blockDim.x + threadIdx.x; q < total; q += (size_t)gridDim.x * blockDim.x) {
-    const size_t l = q / P, p = q - l * P;
-    const float* src = W2 + l * kDbBases * P + p;
-    float acc = 0.f;
+// Finest level of the adjoint, rows, for all eight bases at once: S[l][r][i] =
+// (1/sqrt 8) sum_b (row synthesis of W1[l][b] at (r, i)), bases summed in
+// order, so the per-basis images are never stored.  grid (1, row groups, L).
+template <int TAPS>
+__device__ __forceinline__ float idwt_row_value(const float* __restrict__ src, int b, int i, int H, int m) {
+  const int par = i & 1;
+  float a[TAPS / 2], d[TAPS / 2];
 #pragma unroll
-    for (int b = 0; b < kDbBases; ++b) acc += __ldg(src + b * P);
-    S[q] = kUnionScale * acc;
+  for (int s2 = 0; s2 < TAPS / 2; ++s2) {
+    const int kk = ((i - par - 2 * s2) & m) >> 1;
+    a[s2] = __ldg(src + kk);
+    d[s2] = __ldg(src + H + kk);
+  }
+  float acc = 0.f;
+#pragma unroll
+  for (int s2 = 0; s2 < TAPS / 2; ++s2) {
+    acc = fmaf(c_dbh[b][par + 2 * s2], a[s2], acc);
+    acc = fmaf(c_dbg[b][par + 2 * s2], d[s2], acc);
+  }
+  return acc;
+}
+
+__global__ void k_idwt_rows_sum(const float* __restrict__ W1, float* __restrict__ S, int n) {
+  const int l = blockIdx.z, M = n, H = M >> 1, m = M - 1;
+  const size_t P = (size_t)n * n;
+  const int r1 = min(M, (int)(blockIdx.y + 1) * kRowsPerBlock);
+  for (int r = blockIdx.y * kRowsPerBlock; r < r1; ++r) {
+    const float* src = W1 + (size_t)l * kDbBases * P + (size_t)r * n;
+    for (int i = threadIdx.x; i < M; i += blockDim.x) {
+      float acc = idwt_row_value<2>(src, 0, i, H, m);
+      acc += idwt_row_value<4>(src + P, 1, i, H, m);
+      acc += idwt_row_value<6>(src + 2 * P, 2, i, H, m);
+      acc += idwt_row_value<8>(src + 3 * P, 3, i, H, m);
+      acc += idwt_row_value<10>(src + 4 * P, 4, i, H, m);
+      acc += idwt_row_value<12>(src + 5 * P, 5, i, H, m);
+      acc += idwt_row_value<14>(src + 6 * P, 6, i, H, m);
+      acc += idwt_row_value<16>(src + 7 * P, 7, i, H, m);
+      S[(size_t)l * P + (size_t)r * n + i] = kUnionScale * acc;
+    }
   }
 }
 
@@ -352,11 +382,9 @@ cudaError_t launch_dwt_adjoint(const Geom& g, const DwtArgs& a, cudaStream_t s) 
     const int M = n >> j;
     k_idwt_cols<<<dim3((M + 31) / 32, (M + 8 * kColRun - 1) / (8 * kColRun), Z), dim3(32, 8), 0, s>>>(
         a.U, a.W2, a.W1, n, M, j == g.J - 1);
-    k_idwt_rows<<<dim3(1, (M + kRowsPerBlock - 1) / kRowsPerBlock, Z), 128, 0, s>>>(a.W1, a.W2, n, M);
+    if (j > 0) k_idwt_rows<<<dim3(1, (M + kRowsPerBlock - 1) / kRowsPerBlock, Z), 128, 0, s>>>(a.W1, a.W2, n, M);
+    else k_idwt_rows_sum<<<dim3(1, (M + kRowsPerBlock - 1) / kRowsPerBlock, g.L), 256, 0, s>>>(a.W1, a.S, n);
   }
-  const size_t P = (size_t)n * n, total = (size_t)g.L * P;
-  const int blocks = (int)std::min<size_t>((total + 255) / 256, 4096);
-  k_union_sum<<<blocks, 256, 0, s>>>(a.W2, a.S, P, total);
   return cudaGetLastError();
 }
 
