@@ -187,8 +187,18 @@ __device__ __forceinline__ void fine_pass2(const float* __restrict__ T, int er, 
   }
 }
 
+// Asynchronous 4-byte copy global -> shared (cp.async): a thread issues all
+// of its copies before waiting once, so all of them are in flight together and
+// none passes through registers.
+__device__ __forceinline__ void cp_async4(float* dst, const float* src) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"((uint32_t)__cvta_generic_to_shared(dst)), "l"(src)
+               : "memory");
+}
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_all;" ::: "memory"); }
+
 // Load the square region of side 64 + 2e around the tile (periodic wrap) of a
-// natural-layout plane into X: warps take rows, lanes take columns.
+// natural-layout plane into X: warps take rows, lanes take columns.  (Plain
+// loads: measured faster here than cp.async, which the coarse bands use.)
 template <int HM, int PA>
 __device__ __forceinline__ void load_region(float* __restrict__ X, const float* __restrict__ plane, int e, int n,
                                             int ty0, int tx0) {
@@ -499,23 +509,12 @@ __device__ __forceinline__ void halo_exchange(cg::cluster_group& cl, float* X, i
 }
 
 // Stream one band (RPC x M, row-major with stride M) from global memory into a
-// pitched shared buffer, 8 loads in flight per thread before their stores.
+// pitched shared buffer by asynchronous copies (cp_async_wait() and a barrier
+// before it is read), so the bands of every plane are in flight together.
 __device__ __forceinline__ void band_load(float* __restrict__ dst, int pitch, const float* __restrict__ src,
                                           const CoarseGeo& g) {
   const int c = threadIdx.x & (g.M - 1), rstep = blockDim.x >> g.lgM;
-  for (int rb = threadIdx.x >> g.lgM; rb < g.RPC; rb += 8 * rstep) {
-    float v[8];
-#pragma unroll
-    for (int b = 0; b < 8; ++b) {
-      const int r = rb + b * rstep;
-      v[b] = r < g.RPC ? __ldg(src + (r << g.lgM) + c) : 0.0f;
-    }
-#pragma unroll
-    for (int b = 0; b < 8; ++b) {
-      const int r = rb + b * rstep;
-      if (r < g.RPC) dst[r * pitch + c] = v[b];
-    }
-  }
+  for (int r = threadIdx.x >> g.lgM; r < g.RPC; r += rstep) cp_async4(dst + r * pitch + c, src + (r << g.lgM) + c);
 }
 
 // Both passes of one level at dilation D over the band of X (halo rows
@@ -591,6 +590,7 @@ k_coarse_cl(int n, int J, int j1, int cs, const float* __restrict__ c_in, float*
   if constexpr (MODE == MODE_UPDATE || MODE == MODE_ADJ) {
     for (int j = j1; j <= J; ++j) band_load(us(j), PA, gplane(j), g);
   }
+  cp_async_wait();
   __syncthreads();
   double acc = 0.0;
   if constexpr (MODE != MODE_ADJ) {

@@ -22,8 +22,10 @@
 //                 the same kernel on the flipped, transposed weights,
 //   weight grad  dW[tap][co][ci] = sum_p dz[p][co] a[p + d(tap)][ci]
 //                 (M = co, N = ci, K = voxels), warp-level mma.m16n8k16, one warp per tap.
-// The 1 -> 32 and 32 -> K layers are 27 or 864 multiply-adds per voxel and
-// output; they run on the CUDA cores.  Every reduction over voxels is a
+// The last layer's forward (prediction, or the loss and its gradient d6) is
+// the same tcgen05 kernel with N = 16 (weights of maps K .. 15 zero).  The
+// 1 -> 32 layer and the last layer's gradients (27 or 864 multiply-adds per
+// voxel and output, with float32 d6) run on the CUDA cores.  Every reduction over voxels is a
 // per-block partial sum followed by a fixed-order sum: results do not depend
 // on scheduling.
 #include <cuda.h>            // CUtensorMap (the encoder is reached through the runtime's driver entry point)
@@ -181,14 +183,35 @@ __device__ __forceinline__ uint4 pack8(const float* f) {
 
 // ------------------------------------------------------------------ 32 -> 32 layers on the tensor cores
 
-enum { EPI_RELU = 0, EPI_BIAS = 1, EPI_MASK = 2 };
+// Epilogues of the tcgen05 layer: the 32 -> 32 layers (bias + ReLU, bias, or
+// the ReLU mask of an input gradient) and the last layer (prediction, or loss).
+enum { EPI_RELU = 0, EPI_BIAS = 1, EPI_MASK = 2, EPI_PRED = 3, EPI_LOSS = 4 };
+
+// Per-output-map constants of the last layer (at most kMaxOut maps), by value.
+struct Lam {
+  float v[kMaxOut];
+};
+
+// Operands of the last layer's epilogues (unused by the 32 -> 32 layers).
+struct LastArgs {
+  int K;                      // output maps
+  Lam lam;                    // loss weights
+  const float* s;             // input scale (device scalar)
+  const float* tx;            // EPI_LOSS: target cube [V]
+  const bf16* taux;           // EPI_LOSS: target fields [nz][K-1][ny][nx]
+  float* d6;                  // EPI_LOSS: loss gradient [V][K]
+  double* lpart;              // EPI_LOSS: per-CTA partial sums [grid][K+1]
+  float* out_x;               // EPI_PRED: cube [V]
+  float* out_aux;             // EPI_PRED: fields [nz][K-1][ny][nx]
+};
 
 // ------------------------------------------------------------------ 32 -> 32 layers on tcgen05 (UMMA), fed by TMA
 //
 // One CTA of 128 threads walks output tiles of 128 voxels (one channel, 16
 // rows, 8 columns).  For each tile D[128 voxels][32 features] accumulates in
 // tensor memory over 27 taps x 2 steps of K = 16 by tcgen05.mma (kind::f16,
-// bfloat16 A and B, float32 D, M = 128, N = 32); both operands are read from
+// bfloat16 A and B, float32 D, M = 128, N = 32; N = 16 for the last layer,
+// whose epilogue writes the prediction or the loss terms); both operands are read from
 // shared memory through descriptors in the canonical K-major layout without
 // swizzle (8-row x 16-byte core matrices).
 //
@@ -217,11 +240,16 @@ constexpr int U_HV = 3 * U_HY * U_HX;                       // 540 voxels
 constexpr int U_BOX = U_HV * 16;                            // bytes of one chunk box: 8640
 constexpr int U_CHUNK = 8704;                               // chunk plane stride (128-byte multiple)
 constexpr int U_HALO = 4 * U_CHUNK;                         // 34816
-constexpr int U_W = NTAP * 4 * C * 16;                      // 55296
-constexpr int U_BAR = U_HALO + U_W;                         // 2 mbarriers, then the TMEM address slot
-constexpr int conv05_smem = U_BAR + 64 + 128;               // + alignment slack
-constexpr uint32_t kIdescBf16 = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(C >> 3) << 17) |
-                                ((uint32_t)(128 >> 4) << 24);   // D f32, A/B bf16, K-major, N = 32, M = 128
+constexpr int kLastN = 16;                                  // MMA width of the last layer (K <= 8 maps used)
+template <int EPI> __host__ __device__ constexpr int epi_n() { return EPI >= EPI_PRED ? kLastN : C; }
+// weights: 55296 B (N = 32), 27648 B (N = 16); then 2 mbarriers and the TMEM address slot; alignment slack
+__host__ __device__ constexpr int u_w(int no) { return NTAP * 4 * no * 16; }
+__host__ __device__ constexpr int u_bar(int no) { return U_HALO + u_w(no); }
+__host__ __device__ constexpr int conv05_smem(int no) { return u_bar(no) + 64 + 128; }
+// D f32, A/B bf16, both K-major, N = no, M = 128
+__host__ __device__ constexpr uint32_t idesc_bf16(int no) {
+  return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(no >> 3) << 17) | ((uint32_t)(128 >> 4) << 24);
+}
 constexpr long long kWaitLimit = 1LL << 20;   // polls; each may suspend for a bounded time
 
 __device__ int g_tc_timeouts;
@@ -269,20 +297,24 @@ __device__ __forceinline__ void issue_halo(const HaloMaps& maps, uint32_t s_dst,
 template <int EPI>
 __global__ void __launch_bounds__(128)
 k_conv_tc05(const __grid_constant__ HaloMaps maps, const bf16* __restrict__ wk, const float* __restrict__ bias,
-            const bf16* __restrict__ mask, bf16* __restrict__ out, Dims d, int tiles_x, int tiles_y, int ntiles) {
+            const bf16* __restrict__ mask, bf16* __restrict__ out, Dims d, int tiles_x, int tiles_y, int ntiles,
+            LastArgs la) {
+  constexpr int NO = epi_n<EPI>();
+  constexpr bool kLast = EPI >= EPI_PRED;
   extern __shared__ __align__(128) unsigned char smem[];
+  __shared__ double s_red[32];
   const uint32_t s0 = (smem_u32(smem) + 127u) & ~127u;
   const uint32_t s_halo = s0;
   const uint32_t s_w = s0 + U_HALO;
-  const uint32_t s_full = s0 + U_BAR;              // TMA landed
+  const uint32_t s_full = s0 + u_bar(NO);         // TMA landed
   const uint32_t s_done = s_full + 8;              // MMAs finished
   const uint32_t s_tm = s_full + 16;               // TMEM address written by tcgen05.alloc
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
 
   // weights [tap][co][ci] -> [tap][chunk][co][16 B], once per CTA
-  for (int i = threadIdx.x; i < NTAP * C * 4; i += blockDim.x) {
-    const int c = i & 3, co = (i >> 2) & 31, t = i >> 7;
-    cp_async16(s_w + (uint32_t)(((t * 4 + c) * C + co) * 16), wk + (t * C + co) * C + c * 8, 16);
+  for (int i = threadIdx.x; i < NTAP * NO * 4; i += blockDim.x) {
+    const int c = i & 3, co = (i >> 2) % NO, t = i / (4 * NO);
+    cp_async16(s_w + (uint32_t)(((t * 4 + c) * NO + co) * 16), wk + (t * NO + co) * C + c * 8, 16);
   }
   cp_async_wait_all();
   asm volatile("fence.proxy.async.shared::cta;" ::: "memory");   // generic-proxy writes, read by the MMA
@@ -301,9 +333,18 @@ k_conv_tc05(const __grid_constant__ HaloMaps maps, const bf16* __restrict__ wk, 
   uint32_t tmem;
   asm volatile("ld.shared.b32 %0, [%1];" : "=r"(tmem) : "r"(s_tm) : "memory");
 
-  float bn[C];
+  float bn[NO];
 #pragma unroll
-  for (int c = 0; c < C; ++c) bn[c] = (EPI != EPI_MASK && bias) ? bias[c] : 0.f;
+  for (int c = 0; c < NO; ++c) bn[c] = (EPI != EPI_MASK && bias && (!kLast || c < la.K)) ? bias[c] : 0.f;
+  // last layer: input scale, and this thread's loss sums
+  const float sc = kLast ? *la.s : 1.f;
+  const float inv_sc = 1.0f / sc;
+  const double gs = 2.0 / (double)d.nvox;
+  const size_t plane = (size_t)d.ny * d.nx;
+  double l2 = 0.0;
+  double lsum[kMaxOut];
+#pragma unroll
+  for (int k = 0; k < kMaxOut; ++k) lsum[k] = 0.0;
 
   auto origin = [&](int tile, int& x0, int& y0, int& z0) {
     const int txi = tile % tiles_x, rr = tile / tiles_x;
@@ -337,16 +378,16 @@ k_conv_tc05(const __grid_constant__ HaloMaps maps, const bf16* __restrict__ wk, 
         for (int t = 0; t < NTAP; ++t) {
           const int kz = t / 9, ky = (t / 3) % 3, kx = t % 3;
           const uint32_t a0 = hb + (uint32_t)(((kz * U_HY + ky) * U_HX + kx) * 16);
-          const uint32_t b0 = s_w + (uint32_t)(t * 4 * C * 16);
+          const uint32_t b0 = s_w + (uint32_t)(t * 4 * NO * 16);
 #pragma unroll
           for (int kk = 0; kk < 2; ++kk) {
             const uint64_t ad = umma_desc(a0 + kk * 2 * U_CHUNK, U_CHUNK, U_HX * 16);
-            const uint64_t bd = umma_desc(b0 + kk * 2 * C * 16, C * 16, 8 * 16);
+            const uint64_t bd = umma_desc(b0 + kk * 2 * NO * 16, NO * 16, 8 * 16);
             const uint32_t acc = (t | kk) != 0;
             asm volatile(
                 "{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
                 "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(dt),
-                "l"(ad), "l"(bd), "r"(kIdescBf16), "r"(acc)
+                "l"(ad), "l"(bd), "r"(idesc_bf16(NO)), "r"(acc)
                 : "memory");
           }
         }
@@ -368,46 +409,79 @@ k_conv_tc05(const __grid_constant__ HaloMaps maps, const bf16* __restrict__ wk, 
       pend_ph = (uint32_t)(it + 1) & 1u;
     }
     tc_fence_after();
-    uint32_t r[C];
-    asm volatile(
-        "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
-        "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];\n"
-        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
-          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
-          "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
-          "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
-        : "r"(tmem + ((uint32_t)(warp * 32) << 16)));
-    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
     // row m = 32 warp + lane of D is output voxel (y0 + m / 8, x0 + m % 8) of channel z0
     const int m = warp * 32 + lane;
     const int z = z0, y = y0 + (m >> 3), x = x0 + (m & 7);
-    if (inside(d, z, y, x)) {
-      const size_t base = vox(d, z, y, x) * C;
-      float v[C];
+    const uint32_t taddr = tmem + ((uint32_t)(warp * 32) << 16);
+    if constexpr (!kLast) {
+      uint32_t r[C];
+      asm volatile(
+          "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+          "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];\n"
+          : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+            "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
+            "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
+            "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+          : "r"(taddr));
+      asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+      if (inside(d, z, y, x)) {
+        const size_t base = vox(d, z, y, x) * C;
+        float v[C];
 #pragma unroll
-      for (int c = 0; c < C; ++c) v[c] = __uint_as_float(r[c]);
-      if (EPI == EPI_MASK) {
-        if (mask) {
-          const uint4* mp = reinterpret_cast<const uint4*>(mask + base);
+        for (int c = 0; c < C; ++c) v[c] = __uint_as_float(r[c]);
+        if (EPI == EPI_MASK) {
+          if (mask) {
+            const uint4* mp = reinterpret_cast<const uint4*>(mask + base);
 #pragma unroll
-          for (int q = 0; q < 4; ++q) {
-            float mf[8];
-            unpack8(mp[q], mf);
+            for (int q = 0; q < 4; ++q) {
+              float mf[8];
+              unpack8(mp[q], mf);
 #pragma unroll
-            for (int e = 0; e < 8; ++e)
-              if (!(mf[e] > 0.f)) v[8 * q + e] = 0.f;
+              for (int e = 0; e < 8; ++e)
+                if (!(mf[e] > 0.f)) v[8 * q + e] = 0.f;
+            }
+          }
+        } else {
+#pragma unroll
+          for (int c = 0; c < C; ++c) {
+            v[c] += bn[c];
+            if (EPI == EPI_RELU) v[c] = fmaxf(v[c], 0.f);
           }
         }
-      } else {
+        uint4* o = reinterpret_cast<uint4*>(out + base);
 #pragma unroll
-        for (int c = 0; c < C; ++c) {
-          v[c] += bn[c];
-          if (EPI == EPI_RELU) v[c] = fmaxf(v[c], 0.f);
+        for (int q = 0; q < 4; ++q) o[q] = pack8(v + 8 * q);
+      }
+    } else {
+      // last layer: z_k = D[m][k] + b_k for the K maps (columns K .. 15 hold zero weights)
+      uint32_t r[kLastN];
+      asm volatile(
+          "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];\n"
+          : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+            "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+          : "r"(taddr));
+      asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+      if (inside(d, z, y, x)) {
+        const int K = la.K;
+        const size_t v = vox(d, z, y, x);
+        const size_t a0 = ((size_t)z * (K > 1 ? K - 1 : 1)) * plane + (size_t)y * d.nx + x;
+#pragma unroll
+        for (int k = 0; k < kMaxOut; ++k) {
+          if (k < K) {
+            const float zk = __uint_as_float(r[k]) + bn[k];
+            if constexpr (EPI == EPI_LOSS) {
+              const float tk = k == 0 ? la.tx[v] * inv_sc : __bfloat162float(la.taux[a0 + (size_t)(k - 1) * plane]);
+              const float rk = zk - tk;
+              la.d6[v * K + k] = (float)(gs * la.lam.v[k]) * rk;
+              l2 += (double)la.lam.v[k] * rk * rk;
+              lsum[k] += rk;
+            } else {
+              if (k == 0) la.out_x[v] = fmaxf(sc * zk, 0.f);
+              else la.out_aux[a0 + (size_t)(k - 1) * plane] = fminf(fmaxf(zk, -1.f), 1.f);
+            }
+          }
         }
       }
-      uint4* o = reinterpret_cast<uint4*>(out + base);
-#pragma unroll
-      for (int q = 0; q < 4; ++q) o[q] = pack8(v + 8 * q);
     }
     tc_fence_before();
     __syncthreads();     // the accumulator is read before the next tile's MMAs overwrite it
@@ -418,6 +492,18 @@ k_conv_tc05(const __grid_constant__ HaloMaps maps, const bf16* __restrict__ wk, 
   __syncthreads();
   tc_fence_after();
   if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 32;" ::"r"(tmem) : "memory");
+  if constexpr (EPI == EPI_LOSS) {
+    // lpart[block] = (sum_k lam_k sum_p r_k^2, sum_p r_0, ..., sum_p r_{K-1}), fixed order
+    const double t2 = muffin::block_sum(l2, s_red);
+    if (threadIdx.x == 0) la.lpart[(size_t)blockIdx.x * (la.K + 1)] = t2;
+#pragma unroll
+    for (int k = 0; k < kMaxOut; ++k) {
+      if (k >= la.K) break;
+      __syncthreads();
+      const double tk = muffin::block_sum(lsum[k], s_red);
+      if (threadIdx.x == 0) la.lpart[(size_t)blockIdx.x * (la.K + 1) + 1 + k] = tk;
+    }
+  }
 }
 
 // Weight (and bias) gradient of a 32 -> 32 layer: part[b][tap][co][ci] =
@@ -540,101 +626,6 @@ k_first_fwd(const bf16* __restrict__ a0, const float* __restrict__ w, const floa
       uint4* o = reinterpret_cast<uint4*>(a1 + vox(d, z, y, x) * C);
 #pragma unroll
       for (int q = 0; q < 4; ++q) o[q] = pack8(acc + 8 * q);
-    }
-  }
-}
-
-// Per-output-map constants of the last layer (at most kMaxOut maps), by value.
-struct Lam {
-  float v[kMaxOut];
-};
-
-// Last layer, K output maps: z[k][p] = b[k] + sum_tap sum_ci a5[p + d(tap)][ci] w[tap][ci][k].
-// TRAIN = 0 (prediction): out_x[p] = max(s z[0][p], 0) and, for k >= 1,
-//   out_aux[z][k-1][y][x] = clamp(z[k][p], -1, 1) (the dual fields of Algorithm 1 lie in [-1, 1]).
-// TRAIN = 1 (loss): r0 = z[0] - tx / s, rk = z[k] - taux[z][k-1][y][x];
-//   d6[p][k] = 2 lam_k rk / V (the loss gradient of z[k]);
-//   lpart[block] = (sum_k lam_k sum_p rk^2, sum_p r0, ..., sum_p r_{K-1}).
-template <int TRAIN, int K>
-__global__ void __launch_bounds__(256)
-k_last_fwd(const bf16* __restrict__ a5, const float* __restrict__ w, const float* __restrict__ b,
-           const float* __restrict__ tx, const bf16* __restrict__ taux, Lam lam, const float* __restrict__ s_ptr,
-           float* __restrict__ out_x, float* __restrict__ out_aux, float* __restrict__ d6,
-           double* __restrict__ lpart, Dims d) {
-  extern __shared__ __align__(128) unsigned char smem[];
-  const uint32_t s_a = smem_u32(smem);
-  float* s_w = reinterpret_cast<float*>(smem + HV * ROWB);   // [27][32][K]
-  __shared__ double s_red[32];
-  for (int i = threadIdx.x; i < NTAP * C * K; i += blockDim.x) s_w[i] = w[i];
-  float bias[K];
-#pragma unroll
-  for (int k = 0; k < K; ++k) bias[k] = b[k];
-  const float s = *s_ptr;
-  const float inv_s = 1.0f / s;
-  const size_t plane = (size_t)d.ny * d.nx;
-  int tz, ty, tx_;
-  thread_voxel(tz, ty, tx_);
-  double l2 = 0.0;
-  double lsum[K];
-#pragma unroll
-  for (int k = 0; k < K; ++k) lsum[k] = 0.0;
-  for (int tile = blockIdx.x; tile < d.ntiles; tile += gridDim.x) {
-    int z0, y0, x0;
-    tile_origin(tile, d, z0, y0, x0);
-    __syncthreads();
-    load_map_halo<HZ>(s_a, a5, d, z0 - 1, y0, x0);
-    cp_async_wait_all();
-    __syncthreads();
-    float acc[K];
-#pragma unroll
-    for (int k = 0; k < K; ++k) acc[k] = bias[k];
-#pragma unroll 1
-    for (int t = 0; t < NTAP; ++t) {
-      const int kz = t / 9, ky = (t / 3) % 3, kx = t % 3;
-      const int h = ((tz + kz) * HY + ty + ky) * HX + tx_ + kx;
-#pragma unroll
-      for (int c = 0; c < 4; ++c) {
-        uint4 q;
-        asm volatile("ld.shared.v4.u32 {%0,%1,%2,%3}, [%4];\n"
-                     : "=r"(q.x), "=r"(q.y), "=r"(q.z), "=r"(q.w) : "r"(s_a + swz(h, c)));
-        float f[8];
-        unpack8(q, f);
-        const float* wr = s_w + (t * C + c * 8) * K;
-#pragma unroll
-        for (int e = 0; e < 8; ++e)
-#pragma unroll
-          for (int k = 0; k < K; ++k) acc[k] = fmaf(f[e], wr[e * K + k], acc[k]);
-      }
-    }
-    const int z = z0 + tz, y = y0 + ty, x = x0 + tx_;
-    if (inside(d, z, y, x)) {
-      const size_t v = vox(d, z, y, x);
-      const size_t a0 = ((size_t)z * (K > 1 ? K - 1 : 1)) * plane + (size_t)y * d.nx + x;
-      if (TRAIN) {
-        const double gs = 2.0 / (double)d.nvox;
-#pragma unroll
-        for (int k = 0; k < K; ++k) {
-          const float tk = k == 0 ? tx[v] * inv_s : __bfloat162float(taux[a0 + (size_t)(k - 1) * plane]);
-          const float r = acc[k] - tk;
-          d6[v * K + k] = (float)(gs * lam.v[k]) * r;
-          l2 += (double)lam.v[k] * r * r;
-          lsum[k] += r;
-        }
-      } else {
-        out_x[v] = fmaxf(s * acc[0], 0.f);
-#pragma unroll
-        for (int k = 1; k < K; ++k) out_aux[a0 + (size_t)(k - 1) * plane] = fminf(fmaxf(acc[k], -1.f), 1.f);
-      }
-    }
-  }
-  if (TRAIN) {
-    const double t2 = muffin::block_sum(l2, s_red);
-    if (threadIdx.x == 0) lpart[(size_t)blockIdx.x * (K + 1)] = t2;
-#pragma unroll
-    for (int k = 0; k < K; ++k) {
-      __syncthreads();
-      const double tk = muffin::block_sum(lsum[k], s_red);
-      if (threadIdx.x == 0) lpart[(size_t)blockIdx.x * (K + 1) + 1 + k] = tk;
     }
   }
 }
@@ -857,6 +848,7 @@ struct KernelWeights {
   float* bm;    // [4][32]
   float* w6f;   // [27][32 ci][K]  last layer, forward; bfloat16 values
   float* w6b;   // [27][K][32 ci]  last layer, input gradient
+  bf16* w6t;    // [27][16 co][32 ci]  last layer, tcgen05 operand (rows K .. 15 zero)
   float* b6;    // [K]
 };
 
@@ -894,6 +886,7 @@ __global__ void k_unpack_params(const float* __restrict__ theta, KernelWeights k
     const float r = round_bf16(v);
     kw.w6f[(t * C + ci) * K + k] = r;
     kw.w6b[(t * K + k) * C + ci] = r;
+    kw.w6t[(t * kLastN + k) * C + ci] = __float2bfloat16_rn(v);
   } else {
     kw.b6[j - K * NTAP * C] = v;
   }
@@ -956,15 +949,12 @@ int sm_count() {
   return n;
 }
 
-constexpr int last_fwd_smem(int K) { return HV * ROWB + NTAP * C * K * 4; }
 constexpr int last_bwd_smem(int K) { return K * (NTAP * C + HV) * 4; }
 constexpr int wgrad_last_smem(int K) { return HV * ROWB + TV * K * 4; }
 
 template <int K>
 cudaError_t configure_last() {
   cudaError_t e;
-  if ((e = muffin::allow_max_dyn_smem(k_last_fwd<0, K>)) != cudaSuccess) return e;
-  if ((e = muffin::allow_max_dyn_smem(k_last_fwd<1, K>)) != cudaSuccess) return e;
   if ((e = muffin::allow_max_dyn_smem(k_last_bwd_data<K>)) != cudaSuccess) return e;
   return muffin::allow_max_dyn_smem(k_wgrad_last<K>);
 }
@@ -990,8 +980,10 @@ cudaError_t configure_once(int K) {
   if (!mid_done) {
     mid_done = true;
     if ((mid_err = muffin::allow_max_dyn_smem(k_conv_tc05<EPI_RELU>)) == cudaSuccess &&
-        (mid_err = muffin::allow_max_dyn_smem(k_conv_tc05<EPI_BIAS>)) == cudaSuccess)
-      mid_err = muffin::allow_max_dyn_smem(k_conv_tc05<EPI_MASK>);
+        (mid_err = muffin::allow_max_dyn_smem(k_conv_tc05<EPI_BIAS>)) == cudaSuccess &&
+        (mid_err = muffin::allow_max_dyn_smem(k_conv_tc05<EPI_MASK>)) == cudaSuccess &&
+        (mid_err = muffin::allow_max_dyn_smem(k_conv_tc05<EPI_PRED>)) == cudaSuccess)
+      mid_err = muffin::allow_max_dyn_smem(k_conv_tc05<EPI_LOSS>);
   }
   if (mid_err != cudaSuccess) return mid_err;
   if (K < 1 || K > kMaxOut) return cudaSuccess;
@@ -1049,24 +1041,41 @@ cudaError_t take_launch_error() {
   return e != cudaSuccess ? e : cudaGetLastError();
 }
 
-cudaError_t launch_conv(int epi, const bf16* in, const bf16* wk, const float* bias, const bf16* mask, bf16* out,
-                        const Dims& d, int sms, cudaStream_t st) {
+// Tiles of 128 voxels and the persistent grid of k_conv_tc05 (two CTAs per SM).
+int tc05_tiles(const Dims& d, int& tx, int& ty) {
+  tx = (d.nx + U_TX - 1) / U_TX;
+  ty = (d.ny + U_TY - 1) / U_TY;
+  return tx * ty * d.nz;
+}
+int tc05_grid(const Dims& d, int sms) {
+  int tx, ty;
+  int g = tc05_tiles(d, tx, ty);
+  if (g > 2 * sms) g = 2 * sms;
+  return g < kMaxLossPart ? g : kMaxLossPart;   // also the last layer's loss partial slots
+}
+
+template <int EPI>
+cudaError_t launch_tc05(const bf16* in, const bf16* wk, const float* bias, const bf16* mask, bf16* out,
+                        const Dims& d, int sms, cudaStream_t st, const LastArgs& la) {
   HaloMaps maps;
   const cudaError_t e = halo_maps(in, d, &maps);
   if (e != cudaSuccess) {
     g_launch_err = e;
     return e;
   }
-  const int tx = (d.nx + U_TX - 1) / U_TX, ty = (d.ny + U_TY - 1) / U_TY;
-  const int ntiles = tx * ty * d.nz;
-  const int grid = ntiles < 2 * sms ? ntiles : 2 * sms;   // two CTAs per SM (90 KB of shared memory each)
-  if (epi == EPI_RELU)
-    k_conv_tc05<EPI_RELU><<<grid, 128, conv05_smem, st>>>(maps, wk, bias, mask, out, d, tx, ty, ntiles);
-  else if (epi == EPI_BIAS)
-    k_conv_tc05<EPI_BIAS><<<grid, 128, conv05_smem, st>>>(maps, wk, bias, mask, out, d, tx, ty, ntiles);
-  else
-    k_conv_tc05<EPI_MASK><<<grid, 128, conv05_smem, st>>>(maps, wk, bias, mask, out, d, tx, ty, ntiles);
+  int tx, ty;
+  const int ntiles = tc05_tiles(d, tx, ty);
+  k_conv_tc05<EPI><<<tc05_grid(d, sms), 128, conv05_smem(epi_n<EPI>()), st>>>(maps, wk, bias, mask, out, d, tx, ty,
+                                                                             ntiles, la);
   return cudaGetLastError();
+}
+
+cudaError_t launch_conv(int epi, const bf16* in, const bf16* wk, const float* bias, const bf16* mask, bf16* out,
+                        const Dims& d, int sms, cudaStream_t st) {
+  const LastArgs none{};
+  if (epi == EPI_RELU) return launch_tc05<EPI_RELU>(in, wk, bias, mask, out, d, sms, st, none);
+  if (epi == EPI_BIAS) return launch_tc05<EPI_BIAS>(in, wk, bias, mask, out, d, sms, st, none);
+  return launch_tc05<EPI_MASK>(in, wk, bias, mask, out, d, sms, st, none);
 }
 
 void launch_wgrad_mid(const bf16* a, const bf16* dz, float* part, float* bpart, float* dw, float* db, const Dims& d,
@@ -1137,6 +1146,7 @@ size_t net_layout(muffin_net* n, const Dims& d, int K, int training, char* base)
   kw.bm = (float*)take(4 * C * 4);
   kw.w6f = (float*)take(NTAP * C * K * 4);
   kw.w6b = (float*)take(NTAP * C * K * 4);
+  kw.w6t = (bf16*)take(NTAP * kLastN * C * 2);
   kw.b6 = (float*)take(K * 4);
   float* s = (float*)take(4);
   float* mpart = (float*)take(kMaxLossPart * 4);
@@ -1190,11 +1200,19 @@ void forward_to_a5(muffin_net* n, const float* y) {
 
 bf16* a5_of(muffin_net* n) { return n->training ? n->map(4) : n->map(0); }
 
-template <int K>
+LastArgs last_args(muffin_net* n) {
+  LastArgs la{};
+  la.K = n->K;
+  la.lam = n->lam;
+  la.s = n->s;
+  return la;
+}
+
 void last_predict(muffin_net* n, float* x, float* aux) {
-  const int PL = loss_slots(n->d);
-  k_last_fwd<0, K><<<PL, 256, last_fwd_smem(K), n->st>>>(a5_of(n), n->kw.w6f, n->kw.b6, nullptr, nullptr, n->lam,
-                                                           n->s, x, aux, nullptr, nullptr, n->d);
+  LastArgs la = last_args(n);
+  la.out_x = x;
+  la.out_aux = aux;
+  launch_tc05<EPI_PRED>(a5_of(n), n->kw.w6t, n->kw.b6, nullptr, nullptr, n->d, n->sms, n->st, la);
 }
 
 // Last layer of the training pass: loss, d6, its weight and bias gradients,
@@ -1203,10 +1221,14 @@ template <int K>
 void last_train(muffin_net* n, const float* tx, const bf16* taux, bf16* g5) {
   const Dims& d = n->d;
   bf16* a5 = a5_of(n);
-  const int PL = loss_slots(d);
-  k_last_fwd<1, K><<<PL, 256, last_fwd_smem(K), n->st>>>(a5, n->kw.w6f, n->kw.b6, tx, taux, n->lam, n->s, nullptr,
-                                                           nullptr, n->d6, n->lpart, d);
-  k_loss_final<<<1, K + 1, 0, n->st>>>(n->lpart, PL, K, n->lam, d.nvox, n->loss, n->grad + b_offset(5, K));
+  LastArgs la = last_args(n);
+  la.tx = tx;
+  la.taux = taux;
+  la.d6 = n->d6;
+  la.lpart = n->lpart;
+  launch_tc05<EPI_LOSS>(a5, n->kw.w6t, n->kw.b6, nullptr, nullptr, d, n->sms, n->st, la);
+  k_loss_final<<<1, K + 1, 0, n->st>>>(n->lpart, tc05_grid(d, n->sms), K, n->lam, d.nvox, n->loss,
+                                       n->grad + b_offset(5, K));
   int P = part_slots(d);
   if (P > 2 * n->sms) P = 2 * n->sms;
   k_wgrad_last<K><<<P, 864, wgrad_last_smem(K), n->st>>>(n->d6, a5, n->part, d);
@@ -1239,6 +1261,7 @@ void loss_and_grad(muffin_net* n, const float* y, const float* tx, const bf16* t
 
 void unpack_params(muffin_net* n) {
   const int np = param_count(n->K);
+  cudaMemsetAsync(n->kw.w6t, 0, NTAP * kLastN * C * 2, n->st);
   k_unpack_params<<<(np + 255) / 256, 256, 0, n->st>>>(n->theta, n->kw, n->K);
 }
 
@@ -1321,7 +1344,7 @@ int muffin_net_predict(muffin_net* n, const float* d_dirty, float* d_x, float* d
   if (!d_dirty || !d_x) return fail(n, MUFFIN_ERR_ARG, "NULL cube pointer");
   if (n->K > 1 && !d_aux) return fail(n, MUFFIN_ERR_ARG, "NULL d_aux with more than one output map");
   forward_to_a5(n, d_dirty);
-  MNET_SWITCH_K(n->K, last_predict<KK>(n, d_x, d_aux));
+  last_predict(n, d_x, d_aux);
   return cuda_check(n, "muffin_net_predict");
 }
 

@@ -242,9 +242,9 @@ def warm_start(problem, net: WarmStartNet, net_input: torch.Tensor, keep_state: 
     The network maps ``net_input`` (the dirty cube, or the cube after a few
     passes) to the cube X and, when it has J + 2 output maps, the wavelet
     dual U.  V is kept when ``keep_state`` (else 0), and so is U when the
-    network does not give it.  The method's own state stays the fallback and
-    the judge: the prediction is kept only if the objective of Eqs. 5-6 is
-    lower at the predicted X than at the current one.  Returns what was
+    network does not give it.  The method's own state stays the fallback, and
+    the objective decides: the prediction is kept only if the objective of
+    Eqs. 5-6 is lower at the predicted X than at the current one.  Returns what was
     decided and both objectives."""
     f0, _ = problem.objective()
     x0, u0, v0, it = problem.get_state()
@@ -262,3 +262,54 @@ def warm_start(problem, net: WarmStartNet, net_input: torch.Tensor, keep_state: 
     if not used:
         problem.set_state(x0, u0, v0, it)
     return {"used": bool(used), "f_start": f0, "f_net": f1}
+
+
+# ---------------------------------------------------------------- timing
+
+def _time_main(argv=None) -> None:
+    """Times training steps and predictions of the network on a seeded
+    synthetic cube (uniform input and targets, U targets in [-1, 1]) with CUDA
+    events on the current stream after warm-up, and prints one JSON line."""
+    import argparse
+    import json
+
+    from . import synth
+
+    ap = argparse.ArgumentParser(prog="python -m paper_1602_08847_gb300.net")
+    ap.add_argument("--shape", type=int, nargs=3, default=[64, 256, 256], metavar=("NZ", "NY", "NX"))
+    ap.add_argument("--n-out", type=int, default=6)
+    ap.add_argument("--reps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    args = ap.parse_args(argv)
+    shape, k = tuple(args.shape), args.n_out
+    g = torch.Generator(device="cuda").manual_seed(0)
+    y = torch.rand(shape, device="cuda", generator=g)
+    tx = torch.rand(shape, device="cuda", generator=g)
+    tu = None
+    if k > 1:
+        tu = (torch.rand((shape[0], k - 1) + shape[1:], device="cuda", generator=g) * 2 - 1).to(torch.bfloat16)
+    theta = torch.from_numpy(synth.net_init(0, k)).cuda()
+    weights = [1000.0] + [4.0] + [1.0] * (k - 2) if k > 1 else [1.0]
+    tr = WarmStartNet(shape, training=True, theta=theta, n_out=k, out_weight=weights)
+    inf = WarmStartNet(shape, theta=theta, n_out=k)
+    for _ in range(args.warmup):
+        tr.train_step(y, tx, tu, 1e-3)
+        inf.predict(y)
+    torch.cuda.synchronize()
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+    ev[0].record()
+    for _ in range(args.reps):
+        tr.train_step(y, tx, tu, 1e-3)
+    ev[1].record()
+    for _ in range(args.reps):
+        inf.predict(y)
+    ev[2].record()
+    torch.cuda.synchronize()
+    print(json.dumps({"shape": list(shape), "n_out": k, "reps": args.reps,
+                      "train_step_ms": ev[0].elapsed_time(ev[1]) / max(args.reps, 1),
+                      "predict_ms": ev[1].elapsed_time(ev[2]) / max(args.reps, 1),
+                      "wait_timeouts": wait_timeouts()}))
+
+
+if __name__ == "__main__":
+    _time_main()
