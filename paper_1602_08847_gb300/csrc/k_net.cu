@@ -4,14 +4,15 @@
 // Output map 0 predicts the cube X of Algorithm 1, maps 1 .. K-1 further
 // fields of its state (the planes of the wavelet dual U).
 //
-// Feature maps are [nz][ny][nx][32] bfloat16 (64 bytes per voxel).  Every
-// kernel works on output tiles of 2 x 8 x 16 voxels (channel, row, column)
-// whose inputs, with a one-voxel halo (4 x 10 x 18), are staged in shared
-// memory by cp.async with zero fill outside the cube (the zero padding of the
-// layers).  In shared memory a voxel's 64 bytes are four 16-byte chunks, chunk
-// c of row r stored at chunk c ^ ((r >> 1) & 3): eight consecutive rows read
-// at the same chunk then hit eight different bank groups, which keeps the
-// ldmatrix loads below free of conflicts.
+// Feature maps are [nz][ny][nx][32] bfloat16 (64 bytes per voxel).  The
+// tensor-core kernels (below) walk tiles of 1 x 16 x 8 voxels whose halos
+// arrive by TMA.  The CUDA-core kernels work on output tiles of 2 x 8 x 16
+// voxels (channel, row, column) whose inputs, with a one-voxel halo
+// (4 x 10 x 18), are staged in shared memory by cp.async with zero fill
+// outside the cube (the zero padding of the layers); there a voxel's 64 bytes
+// are four 16-byte chunks, chunk c of row r stored at chunk c ^ ((r >> 1) & 3),
+// so that eight consecutive rows read at the same chunk hit eight different
+// bank groups.
 //
 // The 32 -> 32 layers are implicit GEMMs on the tensor cores, bfloat16 in,
 // float32 accumulate:
@@ -21,13 +22,14 @@
 //   input grad   da[p][ci] = sum_tap sum_co dz[p - d(tap)][co] W[tap][co][ci],
 //                 the same kernel on the flipped, transposed weights,
 //   weight grad  dW[tap][co][ci] = sum_p dz[p][co] a[p + d(tap)][ci]
-//                 (M = co, N = ci, K = voxels), warp-level mma.m16n8k16, one warp per tap.
+//                 (M = (row offset, ci), N = co, K = voxels), tcgen05.mma with nine
+//                 accumulators resident in tensor memory for the CTA's whole run.
 // The last layer's forward (prediction, or the loss and its gradient d6) is
 // the same tcgen05 kernel with N = 16 (weights of maps K .. 15 zero).  The
 // 1 -> 32 layer and the last layer's gradients (27 or 864 multiply-adds per
-// voxel and output, with float32 d6) run on the CUDA cores.  Every reduction over voxels is a
-// per-block partial sum followed by a fixed-order sum: results do not depend
-// on scheduling.
+// voxel and output, with float32 d6) run on the CUDA cores.  Every reduction
+// over voxels is a per-block partial sum followed by a fixed-order sum:
+// results do not depend on scheduling.
 #include <cuda.h>            // CUtensorMap (the encoder is reached through the runtime's driver entry point)
 #include <cuda_runtime.h>
 #include <cuda_bf16.h>
@@ -90,20 +92,6 @@ __device__ __forceinline__ void cp_async16(uint32_t dst, const void* src, int sr
 
 __device__ __forceinline__ void cp_async_wait_all() {
   asm volatile("cp.async.commit_group;\ncp.async.wait_group 0;\n" ::: "memory");
-}
-
-__device__ __forceinline__ void ldsm_x4_t(uint32_t addr, uint32_t& r0, uint32_t& r1, uint32_t& r2, uint32_t& r3) {
-  asm volatile("ldmatrix.sync.aligned.m8n8.x4.trans.shared.b16 {%0,%1,%2,%3}, [%4];\n"
-               : "=r"(r0), "=r"(r1), "=r"(r2), "=r"(r3) : "r"(addr));
-}
-
-// D += A (16x16, row) * B (16x8, col), bfloat16 in, float32 accumulate.
-__device__ __forceinline__ void mma_bf16(float* d, const uint32_t* a, uint32_t b0, uint32_t b1) {
-  asm volatile(
-      "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
-      "{%0,%1,%2,%3};\n"
-      : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
-      : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
 }
 
 __device__ __forceinline__ void tile_origin(int tile, const Dims& d, int& z0, int& y0, int& x0) {
@@ -506,74 +494,196 @@ k_conv_tc05(const __grid_constant__ HaloMaps maps, const bf16* __restrict__ wk, 
   }
 }
 
-// Weight (and bias) gradient of a 32 -> 32 layer: part[b][tap][co][ci] =
-// sum over the voxels of block b's tiles of dz[p][co] a[p + d(tap)][ci].  Grid
-// (P, 3): blockIdx.y is the tap's channel offset, warp w (9 per block) its row
-// and column offsets.  Block (b, 1) warp 0 also sums dz[p][co] into bpart[b][co].
-__global__ void __launch_bounds__(288)
-k_wgrad_tc(const bf16* __restrict__ a, const bf16* __restrict__ dz, float* __restrict__ part,
-           float* __restrict__ bpart, Dims d) {
-  __shared__ __align__(128) unsigned char s_d[TV * ROWB];
-  __shared__ __align__(128) unsigned char s_a[TZ * HY * HX * ROWB];
-  const int kz = blockIdx.y, warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int ky = warp / 3, kx = warp % 3;
-  const int g = lane >> 2, tq = lane & 3;
-  const uint32_t sd = smem_u32(s_d), sa = smem_u32(s_a);
-  const int a_vox = (lane & 7) + ((lane >> 4) & 1) * 8;   // transposed A: rows are voxels
-  const int a_chk = (lane >> 3) & 1;
-  const int b_vox = (lane & 7) + ((lane >> 3) & 1) * 8;
-  const int b_chk = lane >> 4;
-  const bool do_bias = bpart != nullptr && kz == 1 && warp == 0;
-  float acc[2][4][4];
-#pragma unroll
-  for (int mt = 0; mt < 2; ++mt)
-#pragma unroll
-    for (int nt = 0; nt < 4; ++nt)
-#pragma unroll
-      for (int e = 0; e < 4; ++e) acc[mt][nt][e] = 0.f;
-  float bacc = 0.f;
+// ------------------------------------------------------------------ 32 -> 32 weight gradient on tcgen05, fed by TMA
+//
+// dW[tap][co][ci] = sum_p dz[p][co] a[p + d(tap)][ci] as tensor-core products
+// D[m][n] += A[m][k] B[k][n] with k = output voxel p, n = co and
+// m = (ky, ci): one 128-row accumulator per (kz, kx) holds the three row
+// offsets ky = 0..2 of the tap (rows 96..127, "ky = 3", are computed and
+// dropped).  Nine accumulators of 32 float32 columns stay in tensor memory for
+// the CTA's whole run over its tiles; the sums leave TMEM once, at the end.
+//
+// Both operands are MN-major (M or N contiguous: the 8 features of a chunk),
+// canonical layout without swizzle: core matrices of 8 voxels x 16 bytes.
+// The input halo of a tile (3 x 19 x 10 voxels: rows y0-1 .. y0+17, the last
+// one only feeding the dropped rows) lands by one TMA copy as
+// [y][chunk][z][x][16 B] (a 5-D tensor map over (8 features, x, z, chunk, y)
+// with a 16-byte chunk stride): the next 8 rows of m (next chunk, or next ky
+// after four chunks) are 480 B apart, the next 8 voxels of k (next output
+// row) 1920 B.  The tile's own dz lands as [y][chunk][x][16 B]: next 8 co
+// 128 B, next 8 voxels 512 B.
+//
+// Thread 0 keeps a three-stage TMA ring ahead of its MMAs (72 per tile:
+// 9 accumulators x 8 steps of K = 16); warp 1 sums the dz tiles into the bias
+// gradient as they land and releases each stage through an mbarrier.  One CTA
+// per SM (the ring takes 146 KB of shared memory; the accumulators take all
+// 512 TMEM columns).  Every wait is bounded; a CTA that gives up records it in
+// g_tc_timeouts, waits (bounded) for its copies and MMAs in flight, writes
+// nothing and frees its tensor memory.
+constexpr int WG_HY = U_TY + 3;                        // 19 halo rows (one extra for the dropped rows)
+constexpr int WG_A = WG_HY * 4 * 3 * U_HX * 16;        // 36480 B: [19][4][3][10][16 B]
+constexpr int WG_ROW = 4 * 3 * U_HX * 16;              // 1920 B per halo row
+constexpr int WG_B = U_TY * 4 * U_TX * 16;             // 8192 B: [16][4][8][16 B]
+constexpr int WG_STAGE = WG_A + WG_B;                  // 44672 B (a multiple of 128)
+constexpr int WG_NS = 3;                               // ring stages
+constexpr int WG_SLACK = 16384;                        // room past the ring that no descriptor layout can leave
+constexpr int WG_BAR = WG_NS * WG_STAGE + WG_SLACK;    // full[3], done[3], freed[3], fin, TMEM slot
+constexpr int wgrad05_smem = WG_BAR + 128 + 128;
+// D f32, A/B bf16, both MN-major, N = 32, M = 128
+constexpr uint32_t kIdescWgrad = (1u << 4) | (1u << 7) | (1u << 10) | (1u << 15) | (1u << 16) |
+                                 ((uint32_t)(C >> 3) << 17) | ((uint32_t)(128 >> 4) << 24);
 
-  for (int tile = blockIdx.x; tile < d.ntiles; tile += gridDim.x) {
-    int z0, y0, x0;
-    tile_origin(tile, d, z0, y0, x0);
-    __syncthreads();
-    load_map_tile(sd, dz, d, z0, y0, x0);
-    load_map_halo<TZ>(sa, a, d, z0 + kz - 1, y0, x0);
-    cp_async_wait_all();
-    __syncthreads();
-#pragma unroll 2
-    for (int row = 0; row < TZ * TY; ++row) {
-      const int tz = row >> 3, ty = row & 7;
-      uint32_t af[2][4], bfr[4][2];
-#pragma unroll
-      for (int mt = 0; mt < 2; ++mt)
-        ldsm_x4_t(sd + swz(row * TX + a_vox, mt * 2 + a_chk), af[mt][0], af[mt][1], af[mt][2], af[mt][3]);
-      const int hb = (tz * HY + ty + ky) * HX + kx;
-#pragma unroll
-      for (int p = 0; p < 2; ++p)
-        ldsm_x4_t(sa + swz(hb + b_vox, 2 * p + b_chk), bfr[2 * p][0], bfr[2 * p][1], bfr[2 * p + 1][0],
-                  bfr[2 * p + 1][1]);
-#pragma unroll
-      for (int mt = 0; mt < 2; ++mt)
-#pragma unroll
-        for (int nt = 0; nt < 4; ++nt) mma_bf16(acc[mt][nt], af[mt], bfr[nt][0], bfr[nt][1]);
+struct WgradMaps {
+  CUtensorMap a;    // (8, x, z, chunk, y) of the layer input
+  CUtensorMap dz;   // (8, x, chunk, y, z) of the output gradient
+};
+
+__device__ __forceinline__ void wg_issue(const WgradMaps& maps, uint32_t stage, uint32_t bar, int x0, int y0, int z0) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(WG_STAGE) : "memory");
+  asm volatile(
+      "cp.async.bulk.tensor.5d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4, %5, %6}], "
+      "[%7];" ::"r"(stage),
+      "l"(reinterpret_cast<uint64_t>(&maps.a)), "r"(0), "r"(x0 - 1), "r"(z0 - 1), "r"(0), "r"(y0 - 1), "r"(bar)
+      : "memory");
+  asm volatile(
+      "cp.async.bulk.tensor.5d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4, %5, %6}], "
+      "[%7];" ::"r"(stage + WG_A),
+      "l"(reinterpret_cast<uint64_t>(&maps.dz)), "r"(0), "r"(x0), "r"(0), "r"(y0), "r"(z0), "r"(bar)
+      : "memory");
+}
+
+__global__ void __launch_bounds__(128)
+k_wgrad_tc05(const __grid_constant__ WgradMaps maps, float* __restrict__ part, float* __restrict__ bpart, Dims d,
+             int tiles_x, int tiles_y, int ntiles) {
+  extern __shared__ __align__(128) unsigned char smem[];
+  const uint32_t s0 = (smem_u32(smem) + 127u) & ~127u;
+  const uint32_t s_full = s0 + WG_BAR;          // TMA landed, per stage
+  const uint32_t s_done = s_full + 8 * WG_NS;   // MMAs of the stage's tile finished
+  const uint32_t s_freed = s_done + 8 * WG_NS;  // warp 1 has read the stage's dz
+  const uint32_t s_fin = s_freed + 8 * WG_NS;   // every MMA of the CTA finished
+  const uint32_t s_tm = s_fin + 8;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (threadIdx.x == 0) {
+    for (int b = 0; b < WG_NS; ++b) {
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(s_full + 8 * b) : "memory");
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(s_done + 8 * b) : "memory");
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 32;" ::"r"(s_freed + 8 * b) : "memory");
     }
-    if (do_bias) {
-      for (int v = 0; v < TV; ++v)
-        bacc += __bfloat162float(*reinterpret_cast<const bf16*>(s_d + swz(v, lane >> 3) + (lane & 7) * 2));
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(s_fin) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 512;" ::"r"(s_tm) : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  uint32_t tmem;
+  asm volatile("ld.shared.b32 %0, [%1];" : "=r"(tmem) : "r"(s_tm) : "memory");
+
+  auto origin = [&](int tile, int& x0, int& y0, int& z0) {
+    const int txi = tile % tiles_x, rr = tile / tiles_x;
+    x0 = txi * U_TX;
+    y0 = (rr % tiles_y) * U_TY;
+    z0 = rr / tiles_y;
+  };
+  const int nmine = ntiles > (int)blockIdx.x ? (ntiles - (int)blockIdx.x + (int)gridDim.x - 1) / (int)gridDim.x : 0;
+  bool ok = true;
+  float bacc = 0.f;
+  if (threadIdx.x == 0) {
+    // per stage: bit b of `used` once a copy was issued into it, bit b of
+    // `odd` the parity of the number of copies (what an early exit waits for)
+    uint32_t used = 0, odd = 0;
+    for (int i = 0; i < WG_NS && i < nmine; ++i) {
+      int x0, y0, z0;
+      origin(blockIdx.x + i * gridDim.x, x0, y0, z0);
+      wg_issue(maps, s0 + i * WG_STAGE, s_full + 8 * i, x0, y0, z0);
+      used |= 1u << i;
+      odd ^= 1u << i;
+    }
+    for (int it = 0; it < nmine && ok; ++it) {
+      const int s = it % WG_NS;
+      const uint32_t ph = (uint32_t)(it / WG_NS) & 1u;
+      if (!mbar_wait(s_full + 8 * s, ph)) { ok = false; break; }
+      tc_fence_after();
+      const uint32_t sa = s0 + s * WG_STAGE, sb = sa + WG_A;
+#pragma unroll 1
+      for (int acc = 0; acc < 9; ++acc) {
+        const int kz = acc / 3, kx = acc % 3;
+#pragma unroll
+        for (int rp = 0; rp < U_TY / 2; ++rp) {
+          const uint64_t ad = umma_desc(sa + (uint32_t)(2 * rp * WG_ROW + kz * U_HX * 16 + kx * 16), WG_ROW, 3 * U_HX * 16);
+          const uint64_t bd = umma_desc(sb + (uint32_t)(2 * rp * 4 * U_TX * 16), 4 * U_TX * 16, U_TX * 16);
+          const uint32_t accum = (it | rp) != 0;
+          asm volatile(
+              "{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
+              "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem + (uint32_t)(acc * C)),
+              "l"(ad), "l"(bd), "r"(kIdescWgrad), "r"(accum)
+              : "memory");
+        }
+      }
+      asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(s_done + 8 * s)
+                   : "memory");
+      // refill the stage of the previous tile once its MMAs and warp 1 are done with it
+      if (it >= 1 && it - 1 + WG_NS < nmine) {
+        const int sp = (it - 1) % WG_NS;
+        const uint32_t pp = (uint32_t)((it - 1) / WG_NS) & 1u;
+        if (!mbar_wait(s_done + 8 * sp, pp) || !mbar_wait(s_freed + 8 * sp, pp)) { ok = false; break; }
+        int x0, y0, z0;
+        origin(blockIdx.x + (it - 1 + WG_NS) * gridDim.x, x0, y0, z0);
+        wg_issue(maps, s0 + sp * WG_STAGE, s_full + 8 * sp, x0, y0, z0);
+        odd ^= 1u << sp;
+      }
+    }
+    // every MMA issued so far, then the copies still in flight (only after a timeout)
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(s_fin) : "memory");
+    if (!ok)
+      for (int b = 0; b < WG_NS; ++b)
+        if ((used >> b) & 1u) mbar_wait(s_full + 8 * b, ((odd >> b) & 1u) ^ 1u);
+  } else if (warp == 1) {
+    // bias gradient: bacc = sum of dz[p][co = lane] over this CTA's voxels
+    for (int it = 0; it < nmine && ok; ++it) {
+      const int s = it % WG_NS;
+      const uint32_t ph = (uint32_t)(it / WG_NS) & 1u;
+      if (!mbar_wait(s_full + 8 * s, ph)) { ok = false; break; }
+      const unsigned char* b = smem + (s0 - smem_u32(smem)) + s * WG_STAGE + WG_A;
+      const int c = lane >> 3, e = lane & 7;
+#pragma unroll 8
+      for (int v = 0; v < U_TY * U_TX; ++v)
+        bacc += __bfloat162float(*reinterpret_cast<const bf16*>(b + ((v >> 3) * 4 + c) * 128 + (v & 7) * 16 + e * 2));
+      asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(s_freed + 8 * s) : "memory");
     }
   }
-  const int t = kz * 9 + warp;
-  float* pp = part + ((size_t)blockIdx.x * NTAP + t) * (C * C);
+  const bool fin = mbar_wait(s_fin, 0);
+  if (__syncthreads_or(!ok || !fin)) {
+    if (threadIdx.x == 0) atomicAdd(&g_tc_timeouts, 1);
+  } else {
+    tc_fence_after();
+    if (warp < 3) {
+      // lane = ci, TMEM lanes 32 ky .. 32 ky + 31; accumulator (kz, kx) -> tap kz*9 + ky*3 + kx
+#pragma unroll 1
+      for (int q = 0; q < 18; ++q) {            // accumulator q / 2, columns (co) 16 (q % 2) .. + 15
+        const int acc = q >> 1, co0 = (q & 1) * 16;
+        uint32_t r[16];
+        asm volatile(
+            "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];\n"
+            : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+              "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+            : "r"(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(acc * C + co0)));
+        asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+        const int tap = (acc / 3) * 9 + warp * 3 + acc % 3;
+        float* pp = part + ((size_t)blockIdx.x * NTAP + tap) * (C * C) + co0 * C + lane;
 #pragma unroll
-  for (int mt = 0; mt < 2; ++mt)
-#pragma unroll
-    for (int nt = 0; nt < 4; ++nt) {
-      const int co = mt * 16 + g, ci = nt * 8 + tq * 2;
-      *reinterpret_cast<float2*>(pp + co * C + ci) = make_float2(acc[mt][nt][0], acc[mt][nt][1]);
-      *reinterpret_cast<float2*>(pp + (co + 8) * C + ci) = make_float2(acc[mt][nt][2], acc[mt][nt][3]);
+        for (int j = 0; j < 16; ++j) pp[j * C] = __uint_as_float(r[j]);
+      }
     }
-  if (do_bias) bpart[(size_t)blockIdx.x * C + lane] = bacc;
+    if (warp == 1 && bpart) bpart[(size_t)blockIdx.x * C + lane] = bacc;
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 512;" ::"r"(tmem) : "memory");
 }
 
 // ------------------------------------------------------------------ first and last layers (CUDA cores)
@@ -982,8 +1092,9 @@ cudaError_t configure_once(int K) {
     if ((mid_err = muffin::allow_max_dyn_smem(k_conv_tc05<EPI_RELU>)) == cudaSuccess &&
         (mid_err = muffin::allow_max_dyn_smem(k_conv_tc05<EPI_BIAS>)) == cudaSuccess &&
         (mid_err = muffin::allow_max_dyn_smem(k_conv_tc05<EPI_MASK>)) == cudaSuccess &&
-        (mid_err = muffin::allow_max_dyn_smem(k_conv_tc05<EPI_PRED>)) == cudaSuccess)
-      mid_err = muffin::allow_max_dyn_smem(k_conv_tc05<EPI_LOSS>);
+        (mid_err = muffin::allow_max_dyn_smem(k_conv_tc05<EPI_PRED>)) == cudaSuccess &&
+        (mid_err = muffin::allow_max_dyn_smem(k_conv_tc05<EPI_LOSS>)) == cudaSuccess)
+      mid_err = muffin::allow_max_dyn_smem(k_wgrad_tc05);
   }
   if (mid_err != cudaSuccess) return mid_err;
   if (K < 1 || K > kMaxOut) return cudaSuccess;
@@ -1078,11 +1189,49 @@ cudaError_t launch_conv(int epi, const bf16* in, const bf16* wk, const float* bi
   return launch_tc05<EPI_MASK>(in, wk, bias, mask, out, d, sms, st, none);
 }
 
+// The two 5-D tensor maps of k_wgrad_tc05 over [z][y][x][32] bfloat16 maps.
+cudaError_t wgrad_maps(const bf16* a, const bf16* dz, const Dims& d, WgradMaps* maps) {
+  EncodeTiledFn enc = encode_tiled();
+  if (!enc) return cudaErrorNotSupported;
+  const cuuint64_t row = (cuuint64_t)C * 2, line = row * d.nx, plane = line * d.ny;
+  const cuuint32_t estr[5] = {1, 1, 1, 1, 1};
+  {
+    const cuuint64_t dims[5] = {8, (cuuint64_t)d.nx, (cuuint64_t)d.nz, 4, (cuuint64_t)d.ny};
+    const cuuint64_t strides[4] = {row, plane, 16, line};
+    const cuuint32_t box[5] = {8, U_HX, 3, 4, WG_HY};
+    if (enc(&maps->a, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 5, (void*)a, dims, strides, box, estr,
+            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+      return cudaErrorInvalidValue;
+  }
+  {
+    const cuuint64_t dims[5] = {8, (cuuint64_t)d.nx, 4, (cuuint64_t)d.ny, (cuuint64_t)d.nz};
+    const cuuint64_t strides[4] = {row, 16, line, plane};
+    const cuuint32_t box[5] = {8, U_TX, 4, U_TY, 1};
+    if (enc(&maps->dz, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 5, (void*)dz, dims, strides, box, estr,
+            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+      return cudaErrorInvalidValue;
+  }
+  return cudaSuccess;
+}
+
+// Weight and bias gradients of a 32 -> 32 layer: per-CTA partial sums (one
+// CTA per SM, at most part_slots(d) of them), then fixed-order reductions.
 void launch_wgrad_mid(const bf16* a, const bf16* dz, float* part, float* bpart, float* dw, float* db, const Dims& d,
                       int sms, cudaStream_t st) {
+  WgradMaps maps;
+  const cudaError_t e = wgrad_maps(a, dz, d, &maps);
+  if (e != cudaSuccess) {
+    g_launch_err = e;
+    return;
+  }
+  int tx, ty;
+  const int ntiles = tc05_tiles(d, tx, ty);
   int P = part_slots(d);
   if (P > sms) P = sms;
-  k_wgrad_tc<<<dim3(P, 3), 288, 0, st>>>(a, dz, part, bpart, d);
+  if (P > ntiles) P = ntiles;
+  k_wgrad_tc05<<<P, 128, wgrad05_smem, st>>>(maps, part, bpart, d, tx, ty, ntiles);
   k_reduce_part<<<(WMID + 255) / 256, 256, 0, st>>>(part, P, WMID, dw, MAP_MID, 1);
   if (db) k_reduce_part<<<1, 32, 0, st>>>(bpart, P, C, db, MAP_PLAIN, 1);
 }
