@@ -12,12 +12,13 @@
 //   g[t] = (-1)^t h[2p-1-t];
 // its adjoint (= inverse, the bank is orthonormal):
 //   x[i] = sum_{t = i mod 2} h[t] lo[k] + g[t] hi[k],  k = ((i - t) mod M) / 2.
-// Every launch covers all channels and all eight bases (gridDim.z = 8 L);
-// each thread computes a run of outputs (kRowsPerBlock rows per block in the
-// row kernels, kColRun outputs per thread in the column kernels), so blocks
-// live long enough to amortise their scheduling.
-// The levels are short (at most a few MB per basis and channel) and the filters
-// at most 16 taps: the kernels read straight from global memory through L1.
+// Every launch covers all channels and all eight bases (gridDim.z = 8 L).
+// The analysis runs one kernel per level, its row and column passes fused
+// through shared memory (a block owns a slab of columns for all rows).  The
+// adjoint runs a column and a row kernel per level, each thread computing a
+// run of outputs (kColRun per thread, kRowsPerBlock rows per block) so that
+// blocks live long enough to amortise their scheduling; the filters have at
+// most 16 taps and those kernels read straight from global memory through L1.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -144,58 +145,54 @@ constexpr int kColRun = 4;
     default: CALL(16); break;    \
   }
 
-// Analysis, rows of level M: W1[z][r][k] = lo, W1[z][r][M/2 + k] = hi, for
-// the level input (level 0: the shared input cube; else W2[z], the previous
-// level's low-low quadrant).  grid (1, row groups, 8 L).
-template <int TAPS>
-__device__ __forceinline__ void dwt_rows_body(const float* __restrict__ src0, const float* __restrict__ W2,
-                                              float* __restrict__ W1, int n, int M, int level0) {
+// Analysis of one whole level, rows and columns fused through shared memory.
+// A block owns a slab of SC consecutive columns k0 .. k0 + SC - 1 of the
+// row-transformed plane (all lo columns or all hi columns, H % SC == 0):
+// it computes them for all M rows into shared memory (row filter, inputs read
+// through L1), then filters each of its columns: the low-low quadrant feeds
+// the next level (written to `ll`, which the caller alternates between two
+// scratch planes so that no level overwrites the plane it reads), every final
+// coefficient updates U as in dwt_cols_body.  grid (M / SC, 1, 8 L), shared
+// memory M * SC floats.
+template <int MODE, int TAPS>
+__device__ __forceinline__ void dwt_level_body(const float* __restrict__ src0, const float* __restrict__ llin,
+                                               float* __restrict__ ll, float* __restrict__ U, int n, int M, int SC,
+                                               int level0, int last, float kk, float rho, float* __restrict__ sY) {
   const int z = blockIdx.z, b = z & 7, l = z >> 3;
   const int H = M >> 1, m = M - 1;
   const size_t P = (size_t)n * n;
-  const int r1 = min(M, (int)(blockIdx.y + 1) * kRowsPerBlock);
-  for (int r = blockIdx.y * kRowsPerBlock; r < r1; ++r) {
-    const float* src = (level0 ? src0 + (size_t)l * P : W2 + (size_t)z * P) + (size_t)r * n;
-    float* dst = W1 + (size_t)z * P + (size_t)r * n;
-    for (int k = threadIdx.x; k < H; k += blockDim.x) {
-      float x[TAPS];
+  const int k0 = blockIdx.x * SC;
+  const bool hic = k0 >= H;                    // slab of high-pass (detail) columns
+  const int kb = hic ? k0 - H : k0;
+  const float* src = level0 ? src0 + (size_t)l * P : llin + (size_t)z * P;
+  const int lsc = __ffs(SC) - 1;
+  // the basis' filters in registers (constant-memory reads per tap would cost an issue slot each)
+  float hf[TAPS], gf[TAPS];
 #pragma unroll
-      for (int t = 0; t < TAPS; ++t) x[t] = __ldg(src + ((2 * k + t) & m));
-      float lo = 0.f, hi = 0.f;
-#pragma unroll
-      for (int t = 0; t < TAPS; ++t) {
-        lo = fmaf(c_dbh[b][t], x[t], lo);
-        hi = fmaf(c_dbg[b][t], x[t], hi);
-      }
-      dst[k] = lo;
-      dst[H + k] = hi;
-    }
+  for (int t = 0; t < TAPS; ++t) {
+    hf[t] = c_dbh[b][t];
+    gf[t] = c_dbg[b][t];
   }
-}
-
-__global__ void k_dwt_rows(const float* __restrict__ src0, const float* __restrict__ W2, float* __restrict__ W1,
-                           int n, int M, int level0) {
-#define CALL(T) dwt_rows_body<T>(src0, W2, W1, n, M, level0)
-  MUFFIN_DB_DISPATCH(CALL)
-#undef CALL
-}
-
-// Analysis, columns of level M: outputs (k, c) = lo and (M/2 + k, c) = hi of
-// column c of W1[z].  The low-low quadrant feeds the next level (W2[z]) unless
-// this is the last level; every final coefficient w (scaled by 1/sqrt 8)
-// updates U: MODE_UPDATE U <- rho sat(U + k w) + (1 - rho) U, MODE_LINEAR U = w.
-// block (32 columns, 8 outputs), kColRun outputs per thread.
-template <int MODE, int TAPS>
-__device__ __forceinline__ void dwt_cols_body(const float* __restrict__ W1, float* __restrict__ W2,
-                                              float* __restrict__ U, int n, int M, int last, float kk, float rho) {
-  const int z = blockIdx.z, b = z & 7;
-  const int c = blockIdx.x * blockDim.x + threadIdx.x;
-  const int H = M >> 1, m = M - 1;
-  if (c >= M) return;
-  const size_t P = (size_t)n * n;
-  const float* col = W1 + (size_t)z * P + c;
+  for (int idx = threadIdx.x; idx < M * SC; idx += blockDim.x) {
+    const int r = idx >> lsc, j = idx & (SC - 1);
+    const float* row = src + (size_t)r * n;
+    const int base = 2 * (kb + j);
+    // taps in aligned pairs: (2k + t) is even for even t and M is even, so x[t + 1] follows x[t]
+    float x[TAPS];
+#pragma unroll
+    for (int t = 0; t < TAPS; t += 2) {
+      const float2 v = __ldg(reinterpret_cast<const float2*>(row + ((base + t) & m)));
+      x[t] = v.x;
+      x[t + 1] = v.y;
+    }
+    float acc = 0.f;
+#pragma unroll
+    for (int t = 0; t < TAPS; ++t) acc = fmaf(hic ? gf[t] : hf[t], x[t], acc);
+    sY[idx] = acc;
+  }
+  __syncthreads();
   float* Uz = U + (size_t)z * P;
-  auto put = [&](int row, float w) {
+  auto put = [&](int row, int c, float w) {
     float* u = Uz + (size_t)row * n + c;
     w *= kUnionScale;
     if (MODE == MODE_UPDATE) {
@@ -205,29 +202,29 @@ __device__ __forceinline__ void dwt_cols_body(const float* __restrict__ W1, floa
       *u = w;
     }
   };
-#pragma unroll 1
-  for (int j = 0; j < kColRun; ++j) {
-    const int k = (blockIdx.y * kColRun + j) * blockDim.y + threadIdx.y;
-    if (k >= H) break;
+  for (int idx = threadIdx.x; idx < H * SC; idx += blockDim.x) {
+    const int q = idx >> lsc, j = idx & (SC - 1), c = k0 + j;
     float x[TAPS];
 #pragma unroll
-    for (int t = 0; t < TAPS; ++t) x[t] = __ldg(col + (size_t)((2 * k + t) & m) * n);
+    for (int t = 0; t < TAPS; ++t) x[t] = sY[(((2 * q + t) & m) << lsc) + j];
     float lo = 0.f, hi = 0.f;
 #pragma unroll
     for (int t = 0; t < TAPS; ++t) {
-      lo = fmaf(c_dbh[b][t], x[t], lo);
-      hi = fmaf(c_dbg[b][t], x[t], hi);
+      lo = fmaf(hf[t], x[t], lo);
+      hi = fmaf(gf[t], x[t], hi);
     }
-    if (c < H && !last) W2[(size_t)z * P + (size_t)k * n + c] = lo;
-    else put(k, lo);
-    put(H + k, hi);
+    if (!hic && !last) ll[(size_t)z * P + (size_t)q * n + c] = lo;
+    else put(q, c, lo);
+    put(H + q, c, hi);
   }
 }
 
 template <int MODE>
-__global__ void k_dwt_cols(const float* __restrict__ W1, float* __restrict__ W2, float* __restrict__ U, int n,
-                           int M, int last, float kk, float rho) {
-#define CALL(T) dwt_cols_body<MODE, T>(W1, W2, U, n, M, last, kk, rho)
+__global__ void __launch_bounds__(256)
+k_dwt_level(const float* __restrict__ src0, const float* __restrict__ llin, float* __restrict__ ll,
+            float* __restrict__ U, int n, int M, int SC, int level0, int last, float kk, float rho) {
+  extern __shared__ float sY[];
+#define CALL(T) dwt_level_body<MODE, T>(src0, llin, ll, U, n, M, SC, level0, last, kk, rho, sY)
   MUFFIN_DB_DISPATCH(CALL)
 #undef CALL
 }
@@ -245,11 +242,18 @@ __device__ __forceinline__ void idwt_cols_body(const float* __restrict__ U, cons
   const size_t P = (size_t)n * n;
   const float* lo = ((c < H && !coarsest) ? W2 : U) + (size_t)z * P + c;
   const float* hi = U + (size_t)z * P + (size_t)H * n + c;
+  // output rows i of this thread all have the parity of threadIdx.y (blockDim.y is even): its taps in registers
+  const int par = threadIdx.y & 1;
+  float he[TAPS / 2], ge[TAPS / 2];
+#pragma unroll
+  for (int s2 = 0; s2 < TAPS / 2; ++s2) {
+    he[s2] = c_dbh[b][par + 2 * s2];
+    ge[s2] = c_dbg[b][par + 2 * s2];
+  }
 #pragma unroll 1
   for (int j = 0; j < kColRun; ++j) {
     const int i = (blockIdx.y * kColRun + j) * blockDim.y + threadIdx.y;
     if (i >= M) break;
-    const int par = i & 1;
     float a[TAPS / 2], d[TAPS / 2];
 #pragma unroll
     for (int s2 = 0; s2 < TAPS / 2; ++s2) {
@@ -260,8 +264,8 @@ __device__ __forceinline__ void idwt_cols_body(const float* __restrict__ U, cons
     float acc = 0.f;
 #pragma unroll
     for (int s2 = 0; s2 < TAPS / 2; ++s2) {
-      acc = fmaf(c_dbh[b][par + 2 * s2], a[s2], acc);
-      acc = fmaf(c_dbg[b][par + 2 * s2], d[s2], acc);
+      acc = fmaf(he[s2], a[s2], acc);
+      acc = fmaf(ge[s2], d[s2], acc);
     }
     W1[(size_t)z * P + (size_t)i * n + c] = acc;
   }
@@ -275,31 +279,40 @@ __global__ void k_idwt_cols(const float* __restrict__ U, const float* __restrict
 }
 
 // Adjoint, rows of level M: out[z][r][i] from W1[z][r][k] (low) and W1[z][r][M/2 + k] (high).
+// The first half of the block computes the even outputs i = 2u, the second
+// half the odd ones, so that each thread's taps sit in registers and the
+// loads of a warp are consecutive.
 template <int TAPS>
 __device__ __forceinline__ void idwt_rows_body(const float* __restrict__ W1, float* __restrict__ out, int n, int M) {
   const int z = blockIdx.z, b = z & 7;
-  const int H = M >> 1, m = M - 1;
+  const int H = M >> 1;
   const size_t P = (size_t)n * n;
+  const int half = blockDim.x >> 1, par = threadIdx.x >= half, u0 = threadIdx.x - par * half;
+  float he[TAPS / 2], ge[TAPS / 2];
+#pragma unroll
+  for (int s2 = 0; s2 < TAPS / 2; ++s2) {
+    he[s2] = c_dbh[b][par + 2 * s2];
+    ge[s2] = c_dbg[b][par + 2 * s2];
+  }
   const int r1 = min(M, (int)(blockIdx.y + 1) * kRowsPerBlock);
   for (int r = blockIdx.y * kRowsPerBlock; r < r1; ++r) {
     const float* src = W1 + (size_t)z * P + (size_t)r * n;
     float* dst = out + (size_t)z * P + (size_t)r * n;
-    for (int i = threadIdx.x; i < M; i += blockDim.x) {
-      const int par = i & 1;
+    for (int u = u0; u < H; u += half) {
       float a[TAPS / 2], d[TAPS / 2];
 #pragma unroll
       for (int s2 = 0; s2 < TAPS / 2; ++s2) {
-        const int kk = ((i - par - 2 * s2) & m) >> 1;
+        const int kk = (u - s2) & (H - 1);   // ((2u + par - par - 2 s2) mod M) / 2
         a[s2] = __ldg(src + kk);
         d[s2] = __ldg(src + H + kk);
       }
       float acc = 0.f;
 #pragma unroll
       for (int s2 = 0; s2 < TAPS / 2; ++s2) {
-        acc = fmaf(c_dbh[b][par + 2 * s2], a[s2], acc);
-        acc = fmaf(c_dbg[b][par + 2 * s2], d[s2], acc);
+        acc = fmaf(he[s2], a[s2], acc);
+        acc = fmaf(ge[s2], d[s2], acc);
       }
-      dst[i] = acc;
+      dst[2 * u + par] = acc;
     }
   }
 }
@@ -314,40 +327,41 @@ __global__ void k_idwt_rows(const float* __restrict__ W1, float* __restrict__ ou
 // (1/sqrt 8) sum_b (row synthesis of W1[l][b] at (r, i)), bases summed in
 // order, so the per-basis images are never stored.  grid (1, row groups, L).
 template <int TAPS>
-__device__ __forceinline__ float idwt_row_value(const float* __restrict__ src, int b, int i, int H, int m) {
-  const int par = i & 1;
+__device__ __forceinline__ float idwt_row_value(const float* __restrict__ src, int b, int u, int par, int H) {
   float a[TAPS / 2], d[TAPS / 2];
 #pragma unroll
   for (int s2 = 0; s2 < TAPS / 2; ++s2) {
-    const int kk = ((i - par - 2 * s2) & m) >> 1;
+    const int kk = (u - s2) & (H - 1);
     a[s2] = __ldg(src + kk);
     d[s2] = __ldg(src + H + kk);
   }
   float acc = 0.f;
 #pragma unroll
   for (int s2 = 0; s2 < TAPS / 2; ++s2) {
-    acc = fmaf(c_dbh[b][par + 2 * s2], a[s2], acc);
+    acc = fmaf(c_dbh[b][par + 2 * s2], a[s2], acc);   // par is the same across a warp: one broadcast read
     acc = fmaf(c_dbg[b][par + 2 * s2], d[s2], acc);
   }
   return acc;
 }
 
+// Output i = 2u + par: the first half of the block takes the even outputs, the second the odd ones.
 __global__ void k_idwt_rows_sum(const float* __restrict__ W1, float* __restrict__ S, int n) {
-  const int l = blockIdx.z, M = n, H = M >> 1, m = M - 1;
+  const int l = blockIdx.z, M = n, H = M >> 1;
   const size_t P = (size_t)n * n;
+  const int half = blockDim.x >> 1, par = threadIdx.x >= half, u0 = threadIdx.x - par * half;
   const int r1 = min(M, (int)(blockIdx.y + 1) * kRowsPerBlock);
   for (int r = blockIdx.y * kRowsPerBlock; r < r1; ++r) {
     const float* src = W1 + (size_t)l * kDbBases * P + (size_t)r * n;
-    for (int i = threadIdx.x; i < M; i += blockDim.x) {
-      float acc = idwt_row_value<2>(src, 0, i, H, m);
-      acc += idwt_row_value<4>(src + P, 1, i, H, m);
-      acc += idwt_row_value<6>(src + 2 * P, 2, i, H, m);
-      acc += idwt_row_value<8>(src + 3 * P, 3, i, H, m);
-      acc += idwt_row_value<10>(src + 4 * P, 4, i, H, m);
-      acc += idwt_row_value<12>(src + 5 * P, 5, i, H, m);
-      acc += idwt_row_value<14>(src + 6 * P, 6, i, H, m);
-      acc += idwt_row_value<16>(src + 7 * P, 7, i, H, m);
-      S[(size_t)l * P + (size_t)r * n + i] = kUnionScale * acc;
+    for (int u = u0; u < H; u += half) {
+      float acc = idwt_row_value<2>(src, 0, u, par, H);
+      acc += idwt_row_value<4>(src + P, 1, u, par, H);
+      acc += idwt_row_value<6>(src + 2 * P, 2, u, par, H);
+      acc += idwt_row_value<8>(src + 3 * P, 3, u, par, H);
+      acc += idwt_row_value<10>(src + 4 * P, 4, u, par, H);
+      acc += idwt_row_value<12>(src + 5 * P, 5, u, par, H);
+      acc += idwt_row_value<14>(src + 6 * P, 6, u, par, H);
+      acc += idwt_row_value<16>(src + 7 * P, 7, u, par, H);
+      S[(size_t)l * P + (size_t)r * n + 2 * u + par] = kUnionScale * acc;
     }
   }
 }
@@ -363,15 +377,28 @@ __global__ void k_abs_sum(const float* __restrict__ x, size_t n, double* __restr
 
 // ------------------------------------------------------------------ launchers
 
+// Columns per slab of the fused analysis: at most 32, at most 8192 / M (32 KB
+// of shared memory), at most H.
+static int dwt_slab(int M) {
+  int sc = 32;
+  while (sc > 1 && (sc > M / 2 || sc * M > 8192)) sc >>= 1;
+  return sc;
+}
+
 cudaError_t launch_dwt_analysis(const Geom& g, const DwtArgs& a, int mode, cudaStream_t s) {
   const int n = g.n, Z = kDbBases * g.L;
   for (int j = 0; j < g.J; ++j) {
-    const int M = n >> j, H = M >> 1;
-    k_dwt_rows<<<dim3(1, (M + kRowsPerBlock - 1) / kRowsPerBlock, Z), 128, 0, s>>>(a.src, a.W2, a.W1, n, M, j == 0);
-    const dim3 grid((M + 31) / 32, (H + 8 * kColRun - 1) / (8 * kColRun), Z), block(32, 8);
+    const int M = n >> j, sc = dwt_slab(M);
+    // level j reads the low-low plane level j - 1 wrote and writes its own to the other scratch plane
+    const float* llin = (j & 1) ? a.W1 : a.W2;
+    float* ll = (j & 1) ? a.W2 : a.W1;
+    const dim3 grid(M / sc, 1, Z);
+    const size_t sm = (size_t)M * sc * sizeof(float);
     const int last = j == g.J - 1;
-    if (mode == MODE_UPDATE) k_dwt_cols<MODE_UPDATE><<<grid, block, 0, s>>>(a.W1, a.W2, a.U, n, M, last, a.k, a.rho);
-    else k_dwt_cols<MODE_LINEAR><<<grid, block, 0, s>>>(a.W1, a.W2, a.U, n, M, last, 1.f, 1.f);
+    if (mode == MODE_UPDATE)
+      k_dwt_level<MODE_UPDATE><<<grid, 256, sm, s>>>(a.src, llin, ll, a.U, n, M, sc, j == 0, last, a.k, a.rho);
+    else
+      k_dwt_level<MODE_LINEAR><<<grid, 256, sm, s>>>(a.src, llin, ll, a.U, n, M, sc, j == 0, last, 1.f, 1.f);
   }
   return cudaGetLastError();
 }

@@ -825,7 +825,7 @@ int muffin_kernels_per_iteration(const muffin_ctx* ctx) {
   if (!ctx) return 0;
   int n = 0;
   for (int k = 0; k < kNumStages; ++k) n += muffin_stage_bytes(ctx, k) > 0 ? 1 : 0;
-  if (ctx->g.dict && ctx->mu_s != 0.0) n += 4 * ctx->g.J - 1;   // 2J + 1 adjoint and 2J analysis kernels, not 2
+  if (ctx->g.dict && ctx->mu_s != 0.0) n += 3 * ctx->g.J - 2;   // 2J adjoint and J analysis kernels, not 2
   return n;
 }
 
