@@ -802,15 +802,16 @@ k_last_bwd_data(const float* __restrict__ d6, const float* __restrict__ w, const
 }
 
 // part[b][tap][co] = sum_p g1[p][co] a0[p + d(tap)]; bpart[b][co] = sum_p g1[p][co].
-// 864 threads: thread (tap, co).
-__global__ void __launch_bounds__(864)
+// 288 threads: thread (kz, ky, co) keeps the three taps kx = 0..2 of its row
+// offset and walks each tile row along x with a sliding window of three a0
+// values (one a0 and one g1 read per 3 multiply-adds).
+__global__ void __launch_bounds__(288)
 k_wgrad_first(const bf16* __restrict__ a0, const bf16* __restrict__ g1, float* __restrict__ part,
               float* __restrict__ bpart, Dims d) {
   __shared__ float s_h[HV];
   __shared__ __align__(16) float s_g[TV * C];
-  const int t = threadIdx.x >> 5, co = threadIdx.x & 31;
-  const int kz = t / 9, ky = (t / 3) % 3, kx = t % 3;
-  float acc = 0.f, bacc = 0.f;
+  const int co = threadIdx.x & 31, kzy = threadIdx.x >> 5, kz = kzy / 3, ky = kzy % 3;
+  float acc0 = 0.f, acc1 = 0.f, acc2 = 0.f, bacc = 0.f;
   for (int tile = blockIdx.x; tile < d.ntiles; tile += gridDim.x) {
     int z0, y0, x0;
     tile_origin(tile, d, z0, y0, x0);
@@ -826,31 +827,50 @@ k_wgrad_first(const bf16* __restrict__ a0, const bf16* __restrict__ g1, float* _
       dst[1] = make_float4(f[4], f[5], f[6], f[7]);
     }
     __syncthreads();
+#pragma unroll 1
+    for (int row = 0; row < TZ * TY; ++row) {
+      const int tz = row >> 3, ty = row & 7;
+      const float* hr = s_h + ((tz + kz) * HY + ty + ky) * HX;
+      const float* gr = s_g + row * TX * C + co;
+      float w0 = hr[0], w1 = hr[1];
 #pragma unroll 4
-    for (int v = 0; v < TV; ++v) {
-      const int vtx = v & 15, vty = (v >> 4) & 7, vtz = v >> 7;
-      acc = fmaf(s_g[v * C + co], s_h[((vtz + kz) * HY + vty + ky) * HX + vtx + kx], acc);
+      for (int tx = 0; tx < TX; ++tx) {
+        const float w2 = hr[tx + 2], g = gr[tx * C];
+        acc0 = fmaf(g, w0, acc0);
+        acc1 = fmaf(g, w1, acc1);
+        acc2 = fmaf(g, w2, acc2);
+        bacc += g;
+        w0 = w1;
+        w1 = w2;
+      }
     }
-    if (t == 0)
-      for (int v = 0; v < TV; ++v) bacc += s_g[v * C + co];
   }
-  part[(size_t)blockIdx.x * (NTAP * C) + t * C + co] = acc;
-  if (t == 0) bpart[(size_t)blockIdx.x * C + co] = bacc;
+  float* pp = part + (size_t)blockIdx.x * (NTAP * C) + (kz * 9 + ky * 3) * C + co;
+  pp[0] = acc0;
+  pp[C] = acc1;
+  pp[2 * C] = acc2;
+  if (kzy == 0) bpart[(size_t)blockIdx.x * C + co] = bacc;
 }
 
 
-// part[b][tap][ci][k] = sum_p d6[p][k] a5[p + d(tap)][ci].  864 threads: thread (tap, ci).
+// part[b][tap][ci][k] = sum_p d6[p][k] a5[p + d(tap)][ci].  288 threads:
+// thread (kz, ky, ci) keeps the three taps kx = 0..2 of its row offset for
+// all K maps in registers and walks each tile row along x with a sliding
+// window of three a5 values, so that one a5 read and the voxel's K d6 values
+// (read by the whole block at once) feed 3 K multiply-adds.
 template <int K>
-__global__ void __launch_bounds__(864)
+__global__ void __launch_bounds__(288)
 k_wgrad_last(const float* __restrict__ d6, const bf16* __restrict__ a5, float* __restrict__ part, Dims d) {
   extern __shared__ __align__(128) unsigned char smem[];
   const uint32_t sa = smem_u32(smem);
   float* s_d = reinterpret_cast<float*>(smem + HV * ROWB);   // [TV][K]
-  const int t = threadIdx.x >> 5, ci = threadIdx.x & 31;
-  const int kz = t / 9, ky = (t / 3) % 3, kx = t % 3;
-  float acc[K];
+  const int ci = threadIdx.x & 31, kzy = threadIdx.x >> 5, kz = kzy / 3, ky = kzy % 3;
+  const unsigned char* a_ci = smem + (ci & 7) * 2;
+  float acc[3][K];
 #pragma unroll
-  for (int k = 0; k < K; ++k) acc[k] = 0.f;
+  for (int kx = 0; kx < 3; ++kx)
+#pragma unroll
+    for (int k = 0; k < K; ++k) acc[kx][k] = 0.f;
   for (int tile = blockIdx.x; tile < d.ntiles; tile += gridDim.x) {
     int z0, y0, x0;
     tile_origin(tile, d, z0, y0, x0);
@@ -863,18 +883,36 @@ k_wgrad_last(const float* __restrict__ d6, const bf16* __restrict__ a5, float* _
     }
     cp_async_wait_all();
     __syncthreads();
-#pragma unroll 2
-    for (int v = 0; v < TV; ++v) {
-      const int vtx = v & 15, vty = (v >> 4) & 7, vtz = v >> 7;
-      const int h = ((vtz + kz) * HY + vty + ky) * HX + vtx + kx;
-      const float av = __bfloat162float(*reinterpret_cast<const bf16*>(smem + swz(h, ci >> 3) + (ci & 7) * 2));
+#pragma unroll 1
+    for (int row = 0; row < TZ * TY; ++row) {
+      const int tz = row >> 3, ty = row & 7;
+      const int h0 = ((tz + kz) * HY + ty + ky) * HX;   // halo row of this thread's taps
+      auto av = [&](int hx) {
+        return __bfloat162float(*reinterpret_cast<const bf16*>(a_ci + swz(h0 + hx, ci >> 3)));
+      };
+      float w0 = av(0), w1 = av(1);
+#pragma unroll 4
+      for (int tx = 0; tx < TX; ++tx) {
+        const float w2 = av(tx + 2);
+        const float* dv = s_d + (row * TX + tx) * K;
 #pragma unroll
-      for (int k = 0; k < K; ++k) acc[k] = fmaf(s_d[v * K + k], av, acc[k]);
+        for (int k = 0; k < K; ++k) {
+          const float g = dv[k];
+          acc[0][k] = fmaf(g, w0, acc[0][k]);
+          acc[1][k] = fmaf(g, w1, acc[1][k]);
+          acc[2][k] = fmaf(g, w2, acc[2][k]);
+        }
+        w0 = w1;
+        w1 = w2;
+      }
     }
   }
-  float* pp = part + ((size_t)blockIdx.x * (NTAP * C) + t * C + ci) * K;
 #pragma unroll
-  for (int k = 0; k < K; ++k) pp[k] = acc[k];
+  for (int kx = 0; kx < 3; ++kx) {
+    float* pp = part + ((size_t)blockIdx.x * (NTAP * C) + (kz * 9 + ky * 3 + kx) * C + ci) * K;
+#pragma unroll
+    for (int k = 0; k < K; ++k) pp[k] = acc[kx][k];
+  }
 }
 
 // ------------------------------------------------------------------ reductions, input, parameters
@@ -1380,7 +1418,7 @@ void last_train(muffin_net* n, const float* tx, const bf16* taux, bf16* g5) {
                                        n->grad + b_offset(5, K));
   int P = part_slots(d);
   if (P > 2 * n->sms) P = 2 * n->sms;
-  k_wgrad_last<K><<<P, 864, wgrad_last_smem(K), n->st>>>(n->d6, a5, n->part, d);
+  k_wgrad_last<K><<<P, 288, wgrad_last_smem(K), n->st>>>(n->d6, a5, n->part, d);
   k_reduce_part<<<(NTAP * C * K + 255) / 256, 256, 0, n->st>>>(n->part, P, NTAP * C * K, n->grad + w_offset(5),
                                                                MAP_LAST, K);
   const int gsimt = d.ntiles < 4 * n->sms ? d.ntiles : 4 * n->sms;
@@ -1403,7 +1441,7 @@ void loss_and_grad(muffin_net* n, const float* y, const float* tx, const bf16* t
   }
   int P = part_slots(d);
   if (P > 2 * n->sms) P = 2 * n->sms;
-  k_wgrad_first<<<P, 864, 0, n->st>>>(n->a0, g, n->part, n->bpart, d);
+  k_wgrad_first<<<P, 288, 0, n->st>>>(n->a0, g, n->part, n->bpart, d);
   k_reduce_part<<<(NTAP * C + 255) / 256, 256, 0, n->st>>>(n->part, P, NTAP * C, n->grad + w_offset(0), MAP_FIRST, 1);
   k_reduce_part<<<1, 32, 0, n->st>>>(n->bpart, P, C, n->grad + b_offset(0, n->K), MAP_PLAIN, 1);
 }
