@@ -24,6 +24,19 @@ def test_union_spatial_pass_matches_oracle(lib, n, L, J):
     assert np.abs(gu).max() <= 1.0
 
 
+@pytest.mark.parametrize("n,J", [(512, 2), (1024, 1)])
+def test_union_spatial_pass_large_planes(lib, n, J):
+    """Planes of 512 and 1024 pixels, where the fused analysis works on
+    narrower column slabs (16 and 8 columns); step sizes given, so the oracle
+    skips its power methods."""
+    cube = small_cube(n, 1, J, seed=90 + J)
+    p = problem(cube, J, 1, 0.4, 0.0, tau=1e-3, sigma=2.0, dictionary="union")
+    (gx, gu, gv), s = one_pass_both(cube, p, seed=9)
+    assert max_rel(gx, s.X) < TOL1
+    for b in range(8):
+        assert max_rel(gu[:, b], s.U[:, b]) < TOL1, f"basis {b + 1}"
+
+
 def test_union_full_pass_relaxed_weighted(lib):
     cube = small_cube(64, 6, 3, seed=77)
     p = problem(cube, 3, 1, 0.3, 0.8, sigma=1.5, rho=1.3, tau=1e-3, w=np.array([1.0, 2.0, 0.5, 1.5, 1.0, 0.8]),
