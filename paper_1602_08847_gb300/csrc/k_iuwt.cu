@@ -196,35 +196,58 @@ __device__ __forceinline__ void cp_async4(float* dst, const float* src) {
 }
 __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_all;" ::: "memory"); }
 
-// Load the square region of side 64 + 2e around the tile (periodic wrap) of a
-// natural-layout plane into X: warps take rows, lanes take columns.  (Plain
-// loads: measured faster here than cp.async, which the coarse bands use.)
-template <int HM, int PA>
-__device__ __forceinline__ void load_region(float* __restrict__ X, const float* __restrict__ plane, int e, int n,
-                                            int ty0, int tx0) {
-  const int side = kTile + 2 * e, m = n - 1, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
-  for (int r = threadIdx.x >> 5; r < side; r += nw) {
-    const float* srow = plane + (size_t)((ty0 - e + r) & m) * n;
-    float* drow = X + (HM - e + r) * PA + HM - e;
-#pragma unroll 4
-    for (int c = lane; c < side; c += 32) drow[c] = __ldg(srow + ((tx0 - e + c) & m));
+// Load the square region of side 64 + 2E around the tile (periodic wrap) of a
+// natural-layout plane into X: warps take rows, lanes take columns.  The
+// wrapped column offsets of a lane are the same on every row, so they are
+// formed once; the rows are unrolled so that all of a thread's loads are in
+// flight together.
+template <int HM, int PA, int E, int NTH>
+__device__ __forceinline__ void load_region(float* __restrict__ X, const float* __restrict__ plane, int n, int ty0,
+                                            int tx0) {
+  constexpr int SIDE = kTile + 2 * E, NQ = (SIDE + 31) / 32, NW = NTH / 32, RPW = (SIDE + NW - 1) / NW;
+  const int m = n - 1, lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  int cofs[NQ];
+#pragma unroll
+  for (int q = 0; q < NQ; ++q) cofs[q] = (tx0 - E + lane + 32 * q) & m;
+  float* xb = X + (HM - E) * PA + HM - E + lane;
+#pragma unroll
+  for (int k = 0; k < RPW; ++k) {
+    const int r = w + k * NW;
+    if (r < SIDE) {
+      const float* srow = plane + (size_t)((ty0 - E + r) & m) * n;
+#pragma unroll
+      for (int q = 0; q < NQ; ++q)
+        if (lane + 32 * q < SIDE) xb[r * PA + 32 * q] = __ldg(srow + cofs[q]);
+    }
   }
 }
 
-// Same from a class-permuted plane (stride 2^lgs).
-template <int HM, int PA>
-__device__ __forceinline__ void load_region_class(float* __restrict__ X, const float* __restrict__ plane, int e, int n,
+// Same from a class-permuted plane (stride 2^lgs): element (gy, gx) sits at
+// ((gy & s1) s + (gx & s1)) mc^2 + (gy >> lgs) mc + (gx >> lgs), a row part
+// plus a column part.
+template <int HM, int PA, int E, int NTH>
+__device__ __forceinline__ void load_region_class(float* __restrict__ X, const float* __restrict__ plane, int n,
                                                   int lgs, int ty0, int tx0) {
-  const int side = kTile + 2 * e, m = n - 1, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+  constexpr int SIDE = kTile + 2 * E, NQ = (SIDE + 31) / 32, NW = NTH / 32, RPW = (SIDE + NW - 1) / NW;
+  const int m = n - 1, lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   const int s1 = (1 << lgs) - 1, mc = n >> lgs;
-  for (int r = threadIdx.x >> 5; r < side; r += nw) {
-    const int gy = (ty0 - e + r) & m;
-    const float* srow = plane + ((size_t)(gy & s1) << lgs) * mc * mc + (size_t)(gy >> lgs) * mc;
-    float* drow = X + (HM - e + r) * PA + HM - e;
-#pragma unroll 4
-    for (int c = lane; c < side; c += 32) {
-      const int gx = (tx0 - e + c) & m;
-      drow[c] = __ldg(srow + (size_t)(gx & s1) * mc * mc + (gx >> lgs));
+  const size_t mc2 = (size_t)mc * mc;
+  size_t cofs[NQ];
+#pragma unroll
+  for (int q = 0; q < NQ; ++q) {
+    const int gx = (tx0 - E + lane + 32 * q) & m;
+    cofs[q] = (size_t)(gx & s1) * mc2 + (gx >> lgs);
+  }
+  float* xb = X + (HM - E) * PA + HM - E + lane;
+#pragma unroll
+  for (int k = 0; k < RPW; ++k) {
+    const int r = w + k * NW;
+    if (r < SIDE) {
+      const int gy = (ty0 - E + r) & m;
+      const float* srow = plane + ((size_t)(gy & s1) << lgs) * mc2 + (size_t)(gy >> lgs) * mc;
+#pragma unroll
+      for (int q = 0; q < NQ; ++q)
+        if (lane + 32 * q < SIDE) xb[r * PA + 32 * q] = __ldg(srow + cofs[q]);
     }
   }
 }
@@ -286,11 +309,11 @@ __device__ __forceinline__ void fine_analysis_level(float*& A, float*& B, float*
 }
 
 template <int GEN, int J1, int MODE>
-__global__ void __launch_bounds__(kFineThreads)
+__global__ void __launch_bounds__(kFineThreads, 2)
 k_fine_analysis(int n, int J, IuwtArgs a) {
   constexpr int NTH = kFineThreads;
   using G = FineGeo<GEN, J1>;
-  constexpr int HM = G::HM, SD = G::SD, PA = G::PA;
+  constexpr int HM = G::HM, PA = G::PA;
   extern __shared__ __align__(16) float sm[];
   __shared__ double red[32];
   float* A = sm;
@@ -299,7 +322,6 @@ k_fine_analysis(int n, int J, IuwtArgs a) {
   float* B = Bi + G::NI;   // generation 2 only
   const int l = blockIdx.z, ty0 = blockIdx.y * kTile, tx0 = blockIdx.x * kTile;
   const size_t P = (size_t)n * n;
-  const int m = n - 1;
   double acc = 0.0;
   // prefetch the tile's dual values; their latency hides behind the filtering
   float up[J1 + 1][8];
@@ -316,7 +338,7 @@ k_fine_analysis(int n, int J, IuwtArgs a) {
         up[J1][k] = __ldg(a.U + ((size_t)l * (J + 1) + J) * P + class_index(ty0 + ri, tx0 + ci, n, J1));
     }
   }
-  load_region<HM, PA>(A, a.D + (size_t)l * P, HM, n, ty0, tx0);
+  load_region<HM, PA, HM, NTH>(A, a.D + (size_t)l * P, n, ty0, tx0);
   __syncthreads();
   if constexpr (J1 > 0) fine_analysis_level<GEN, J1, MODE, 0>(A, B, T, Bi, up, a, n, J, l, ty0, tx0, acc);
   // c_{j1} on the tile: last plane (J == j1) or hand-off to the coarse levels
@@ -352,6 +374,9 @@ __device__ __forceinline__ void fine_adjoint_level(float*& R, float*& Ub, float*
   const int m = n - 1;
   if constexpr (J0 > 0) {
     const float* Un = a.U + ((size_t)l * (J + 1) + J0 - 1) * (size_t)n * n;
+    int cofs[NQ];
+#pragma unroll
+    for (int q = 0; q < NQ; ++q) cofs[q] = (tx0 - eun + lane + 32 * q) & m;
 #pragma unroll
     for (int k = 0; k < NR; ++k) {
       const int r = wrp + NW * k;
@@ -359,7 +384,7 @@ __device__ __forceinline__ void fine_adjoint_level(float*& R, float*& Ub, float*
 #pragma unroll
       for (int q = 0; q < NQ; ++q) {
         const int c = lane + 32 * q;
-        pf[k][q] = (r < sidn && c < sidn) ? __ldg(srow + ((tx0 - eun + c) & m)) : 0.0f;
+        pf[k][q] = (r < sidn && c < sidn) ? __ldg(srow + cofs[q]) : 0.0f;
       }
     }
   }
@@ -405,9 +430,8 @@ k_fine_adjoint(int n, int J, const float* __restrict__ rin, size_t rin_stride, I
   float* T = Ub + G::NA;
   const int l = blockIdx.z, ty0 = blockIdx.y * kTile, tx0 = blockIdx.x * kTile;
   const size_t P = (size_t)n * n;
-  const int m = n - 1;
-  load_region_class<HM, PA>(R, rin + (size_t)l * rin_stride, halo_r(J1), n, J1, ty0, tx0);
-  load_region<HM, PA>(Ub, a.U + ((size_t)l * (J + 1) + J1 - 1) * P, halo_u(GEN, J1 - 1), n, ty0, tx0);
+  load_region_class<HM, PA, halo_r(J1), NTH>(R, rin + (size_t)l * rin_stride, n, J1, ty0, tx0);
+  load_region<HM, PA, halo_u(GEN, J1 - 1), NTH>(Ub, a.U + ((size_t)l * (J + 1) + J1 - 1) * P, n, ty0, tx0);
   __syncthreads();
   fine_adjoint_level<GEN, J1, J1 - 1, NTH>(R, Ub, T, a, n, J, l, ty0, tx0);
   const int ci = int_col();
