@@ -588,13 +588,24 @@ __device__ __forceinline__ void coarse_filter(cg::cluster_group& cl, float* X, f
   }
 }
 
-template <int GEN, int MODE>
+// MT > 0: a single-block instance for class sub-images of MT x MT (cs = 1),
+// whose geometry is known at compile time, so that every shared-memory stencil
+// address is a base plus immediate offsets.
+template <int GEN, int MODE, int MT = 0>
 __global__ void __launch_bounds__(kCoarseThreads)
 k_coarse_cl(int n, int J, int j1, int cs, const float* __restrict__ c_in, float* __restrict__ r_out,
             float* __restrict__ U, float k, float rho, double* __restrict__ partials) {
   cg::cluster_group cl = cg::this_cluster();
   const int rank = (int)cl.block_rank();
-  const CoarseGeo g = coarse_geo(n, J, j1, cs);
+  CoarseGeo g = coarse_geo(n, J, j1, cs);
+  if constexpr (MT > 0) {
+    constexpr int lg = MT == 32 ? 5 : MT == 64 ? 6 : 7;
+    g.M = MT; g.RPC = MT; g.PA = MT + 1; g.PT = MT + 1; g.lgM = lg; g.lgR = lg;
+    g.NA = (size_t)(MT + 2 * g.HR) * (MT + 1);
+    g.NT = (size_t)MT * (MT + 1);
+    g.NU = (size_t)MT * (MT + 1);
+    cs = 1;
+  }
   extern __shared__ __align__(16) float sm[];
   __shared__ double red[32];
   float* A = sm;
@@ -943,6 +954,9 @@ static cudaError_t coarse_n(const Geom& g, const float* c_in, float* r_out, floa
     attr[0].val.clusterDim.z = 1;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
+    if (g.cs == 1 && (g.n >> g.j1) == 64)
+      return cudaLaunchKernelEx(&cfg, k_coarse_cl<GEN, MODE, 64>, g.n, g.J, g.j1, g.cs, c_in, r_out, U, k, rho,
+                                partials);
     return cudaLaunchKernelEx(&cfg, k_coarse_cl<GEN, MODE>, g.n, g.J, g.j1, g.cs, c_in, r_out, U, k, rho, partials);
   }
   const int M = g.n >> g.j1;
@@ -1008,6 +1022,8 @@ template <int GEN> static cudaError_t cfg_gen(Geom& g) {
   if (g.J > g.j1) {
     SET((k_coarse<GEN, 0>)) SET((k_coarse<GEN, 1>)) SET((k_coarse<GEN, 2>)) SET((k_coarse<GEN, 3>))
     SET((k_coarse_cl<GEN, 0>)) SET((k_coarse_cl<GEN, 1>)) SET((k_coarse_cl<GEN, 2>)) SET((k_coarse_cl<GEN, 3>))
+    SET((k_coarse_cl<GEN, 0, 64>)) SET((k_coarse_cl<GEN, 1, 64>)) SET((k_coarse_cl<GEN, 2, 64>))
+    SET((k_coarse_cl<GEN, 3, 64>))
     // cluster split: the smallest whose blocks fit three, two, then one per SM; MUFFIN_COARSE_CLUSTER
     // (1, 2, 4 or 8) forces a size for tuning when it fits
     if (const char* env = getenv("MUFFIN_COARSE_CLUSTER")) {
