@@ -126,18 +126,6 @@ __device__ __forceinline__ void load_map_halo(uint32_t s, const bf16* __restrict
   }
 }
 
-// The tile's own TV voxels of a map, row r = (tz*TY + ty)*TX + tx.
-__device__ __forceinline__ void load_map_tile(uint32_t s, const bf16* __restrict__ g, const Dims& d, int z0, int y0,
-                                              int x0) {
-  for (int i = threadIdx.x; i < TV * 4; i += blockDim.x) {
-    const int c = i & 3, r = i >> 2;
-    const int gz = z0 + (r >> 7), gy = y0 + ((r >> 4) & 7), gx = x0 + (r & 15);
-    const bool ok = inside(d, gz, gy, gx);
-    const bf16* src = ok ? g + vox(d, gz, gy, gx) * C + c * 8 : g;
-    cp_async16(s + swz(r, c), src, ok ? 16 : 0);
-  }
-}
-
 // Scalar field halo (float32 cube or bfloat16 single-feature map) into s[h], zero outside.
 template <typename T>
 __device__ __forceinline__ void load_scalar_halo(float* s, const T* __restrict__ g, const Dims& d, int z0, int y0,

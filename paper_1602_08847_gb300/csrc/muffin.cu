@@ -22,7 +22,6 @@ const char* kStageNames[kNumStages] = {"iuwt_fine_adjoint", "fft_rows_fwd", "fft
                                        "iuwt_fine_analysis", "iuwt_coarse", "spectral_dct"};
 
 bool is_pow2(int v) { return v > 0 && (v & (v - 1)) == 0; }
-int ilog2(int v) { int r = 0; while ((1 << r) < v) ++r; return r; }
 
 // Split j1 (levels below it run on halo tiles, the others on class
 // sub-images).  Measured on GB300: the largest split whose coarse sub-image
