@@ -35,7 +35,7 @@ def parse():
     ap.add_argument("--steps", type=int, default=100)
     ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", default="muffin", choices=["muffin", "reference"])
-    ap.add_argument("--config", default="D")
+    ap.add_argument("--config", default="512x512x256")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-ttt", action="store_true")
@@ -262,7 +262,7 @@ def main():
     # four uneven cubes advanced together: one graph launch per pass (muffin_batch) vs one by one
     # the comparison dictionary of Sec. 4: the same pass with W_s = union of eight Daubechies bases
     if not args.no_union and rank == 0:
-        cu = synth.make_cube("B")
+        cu = synth.make_cube("256x256x64")
         mu = Muffin(torch.from_numpy(cu.dirty).cuda(), torch.from_numpy(cu.psf).cuda(), nscales=4,
                     mu_s=0.25, mu_l=3.0, dictionary="union")
         mi = Muffin(torch.from_numpy(cu.dirty).cuda(), torch.from_numpy(cu.psf).cuda(), nscales=4,
@@ -289,7 +289,7 @@ def main():
         from paper_1602_08847_gb300.muffin import Batch
         ms = []
         vox_c = 0
-        for name in ("C0", "C1", "C2", "C3"):
+        for name in ("128x128x16", "256x256x32", "512x512x64", "1024x1024x8"):
             cc = synth.make_cube(name)
             ms.append(Muffin(torch.from_numpy(cc.dirty).cuda(), torch.from_numpy(cc.psf).cuda(),
                              nscales=cc.cfg.nscales, gen=1, mu_s=0.25, mu_l=3.0))
@@ -328,7 +328,7 @@ def main():
     # state and from the learned warm start (the committed network, if present)
     if not args.no_ttt and rank == 0:
         from paper_1602_08847_gb300 import warmstart as ws
-        cb = synth.make_cube("B")
+        cb = synth.make_cube("256x256x64")
         net, meta = ws.load_committed()
         r = ws.evaluate_one(net, cb.dirty, cb.psf, 4, input_passes=meta.get("input_passes", 0) if net else 0)
         ttt = {"workload": "256x256x64, 40 sources, 60 antennas, J=4 (seed 2, not a training seed)",

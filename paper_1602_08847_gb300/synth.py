@@ -54,13 +54,13 @@ class CubeConfig:
 
 # The workloads (sizes, source/antenna counts, scales, seeds).
 CONFIGS = {
-    "A": CubeConfig("A", n=64, nchan=8, n_src=5, n_ant=20, nscales=3, seed=1, iters=100),
-    "B": CubeConfig("B", n=256, nchan=64, n_src=40, n_ant=60, nscales=4, seed=2, iters=200),
-    "C0": CubeConfig("C0", n=128, nchan=16, n_src=40, n_ant=60, nscales=4, seed=11),
-    "C1": CubeConfig("C1", n=256, nchan=32, n_src=40, n_ant=60, nscales=4, seed=12),
-    "C2": CubeConfig("C2", n=512, nchan=64, n_src=40, n_ant=60, nscales=4, seed=13),
-    "C3": CubeConfig("C3", n=1024, nchan=8, n_src=40, n_ant=60, nscales=4, seed=14),
-    "D": CubeConfig("D", n=512, nchan=256, n_src=200, n_ant=128, nscales=5,
+    "64x64x8": CubeConfig("64x64x8", n=64, nchan=8, n_src=5, n_ant=20, nscales=3, seed=1, iters=100),
+    "256x256x64": CubeConfig("256x256x64", n=256, nchan=64, n_src=40, n_ant=60, nscales=4, seed=2, iters=200),
+    "128x128x16": CubeConfig("128x128x16", n=128, nchan=16, n_src=40, n_ant=60, nscales=4, seed=11),
+    "256x256x32": CubeConfig("256x256x32", n=256, nchan=32, n_src=40, n_ant=60, nscales=4, seed=12),
+    "512x512x64": CubeConfig("512x512x64", n=512, nchan=64, n_src=40, n_ant=60, nscales=4, seed=13),
+    "1024x1024x8": CubeConfig("1024x1024x8", n=1024, nchan=8, n_src=40, n_ant=60, nscales=4, seed=14),
+    "512x512x256": CubeConfig("512x512x256", n=512, nchan=256, n_src=200, n_ant=128, nscales=5,
                     point_frac=0.1, seed=3, iters=100),
 }
 

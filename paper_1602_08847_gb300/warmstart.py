@@ -221,7 +221,7 @@ def _seeds(spec: str):
 
 def main():
     ap = argparse.ArgumentParser()
-    ap.add_argument("--config", default="B")
+    ap.add_argument("--config", default="256x256x64")
     ap.add_argument("--train-seeds", default="1000:3000")
     ap.add_argument("--eval-seeds", default="5000:5200")
     ap.add_argument("--iters", type=int, default=500)

@@ -43,7 +43,7 @@ def _gpu_pass(cube, tau, sigma, x, u, v):
     return out
 
 
-@pytest.mark.parametrize("name,chans", [("D", [0, 77, 255]), ("B", [0, 31, 63])])
+@pytest.mark.parametrize("name,chans", [("512x512x256", [0, 77, 255]), ("256x256x64", [0, 31, 63])])
 def test_full_size_pass_on_sampled_channels(lib, name, chans):
     """X and every plane of U of sampled channels after one pass from a random state."""
     cube, hh, tau, sigma = _setup(name)
@@ -63,7 +63,7 @@ def test_full_size_pass_on_sampled_channels(lib, name, chans):
             assert max_rel(gu[l, j].astype(np.float64), ut[j]) < TOL1, (l, j)
 
 
-@pytest.mark.parametrize("name", ["D", "B"])
+@pytest.mark.parametrize("name", ["512x512x256", "256x256x64"])
 def test_full_size_pass_on_sampled_pixels(lib, name):
     """V (the spectral dual) at sampled pixels after one pass, with U = 0 so that
     the spatial adjoint vanishes and every channel's X~ at a pixel follows from

@@ -76,7 +76,7 @@ def test_100_passes_64x64x8(lib, gen):
     """The 64 x 64 x 8 workload (5 sources, 20 antennas, J = 3, 100 passes from
     zero): rel L2 of X <= 1e-4 and relative objective <= 1e-6 against FP64."""
     from paper_1602_08847_gb300 import synth
-    cube = synth.make_cube("A")
+    cube = synth.make_cube("64x64x8")
     p = problem(cube, 3, gen, 0.25, 3.0)
     m = gpu_solver(cube, p)
     m.iterate(100)

@@ -30,7 +30,7 @@ def committed(lib):
 @pytest.mark.parametrize("seed", [5198, 5199])
 def test_warm_start_reaches_tolerance_sooner(committed, seed):
     ws, net, meta = committed
-    _, y, h = synth.cube_arrays(("B", seed))
+    _, y, h = synth.cube_arrays(("256x256x64", seed))
     r = ws.evaluate_one(net, y, h, 4, input_passes=meta["input_passes"])
     zero, warm = r["zero"], r["net"]
     assert zero["passes"] is not None and warm["passes"] is not None
@@ -44,7 +44,7 @@ def test_rejected_prediction_leaves_the_state_alone(committed):
     is not used, and the state it found is restored."""
     ws, net, meta = committed
     from paper_1602_08847_gb300.net import WarmStartNet, warm_start
-    _, y, h = synth.cube_arrays(("B", 5197))
+    _, y, h = synth.cube_arrays(("256x256x64", 5197))
     yd, hd = torch.from_numpy(y).cuda(), torch.from_numpy(h).cuda()
     m = ws.problem(yd, hd, 4)
     m.iterate(30)
