@@ -280,6 +280,73 @@ def test_successive_differences_shrink_in_condat_metric(gen):
         prev, s = d, s2
 
 
+def _relaxed_tiny_problem(case, rho):
+    """The 8x8x2 problem of tests/golden with steps that admit rho up to delta = 1.6:
+    tau = 1/(2 beta) and sigma ||L||^2 = (1/tau - beta/2)/2, so 1/tau - sigma ||L||^2 = 1.25 beta."""
+    with open(os.path.join(GOLDEN, f"tiny_minimizer_{case}.json")) as f:
+        g = json.load(f)
+    c = g["case"]
+    y, psf, _ = tiny_inputs()
+    p = mo.make_problem(y, psf, c["J"], gen=c["gen"], mu_s=c["mu_s"], mu_l=c["mu_l"], tau=1.0)
+    beta = float(np.max(np.abs(p.hhat) ** 2))
+    l2 = mo.dual_norm2(p.mu_s, p.mu_l, mo.iuwt_norm2_closed_form(8, p.J, p.gen))
+    p.tau = 0.5 / beta
+    p.sigma = 0.5 * (1.0 / p.tau - beta / 2) / l2
+    delta = 2.0 - 0.5 * beta / (1.0 / p.tau - p.sigma * l2)
+    assert 0.0 < rho < delta
+    p.rho = rho
+    return p, g
+
+
+@pytest.mark.parametrize("rho", [0.6, 1.5])
+@pytest.mark.parametrize("case", ["gen1_J1", "gen2_J1"])
+def test_relaxed_iteration_reaches_independent_minimiser(case, rho):
+    """Alg. 1, relaxation step (Sec. 3, Eqs. 12 and 14): for any rho in (0, delta) the
+    relaxed iteration has the fixed points of the unrelaxed one, so it must end at the
+    minimiser that dense ADMM and smoothed projected gradient found (tests/golden).
+    At rho = 1.5 a relaxation line with rho and 1 - rho swapped weighs the new iterate
+    by -0.5 and diverges."""
+    p, g = _relaxed_tiny_problem(case, rho)
+    s = mo.iterate(p, mo.zero_state(p), 2000)
+    x_ref = np.array(g["x"])
+    assert np.linalg.norm(s.X.ravel() - x_ref) / np.linalg.norm(x_ref) < 1e-6
+    assert abs(mo.objective(p, s.X) - g["objective"]) / g["objective"] < 1e-9
+
+
+@pytest.mark.parametrize("rho", [0.6, 1.5])
+def test_relaxed_successive_differences_shrink_in_condat_metric(rho):
+    """For rho < delta the relaxed pass (1 - rho) I + rho T is still averaged in Condat's
+    metric P (a Krasnosel'skii-Mann iteration), so ||z_{k+1} - z_k||_P never grows."""
+    p, _ = _relaxed_tiny_problem("gen1_J1", rho)
+    s = mo.zero_state(p)
+    prev, first = None, None
+    for _ in range(300):
+        s2 = mo.iterate(p, s, 1)
+        d = _p_norm2(p, s2.X - s.X, s2.U - s.U, s2.V - s.V)
+        first = d if first is None else first
+        if prev is not None and d > 1e-18 * first:
+            assert d <= prev * (1 + 1e-9)
+        prev, s = d, s2
+
+
+@pytest.mark.parametrize("rho", [0.6, 1.3, 1.5])
+def test_relaxed_primal_trajectory_closed_form(rho):
+    """H = I and mu_s = mu_lambda = 0, from X = 0: where y > 0 the relaxed primal step is
+    X <- X + rho tau (y - X), so X_k = y (1 - (1 - rho tau)^k) exactly; where y <= 0, X
+    stays 0; the duals never move.  This fixes the weight rho of the new iterate in the
+    primal relaxation line, which the fixed point alone does not."""
+    L, n, tau = 2, 8, 0.5
+    y = rnd((L, n, n), 23)
+    p = mo.Problem(y=y, hhat=mo.psf_multiplier(_delta_psf(L, n)), J=1, mu_s=0.0, mu_l=0.0,
+                   tau=tau, sigma=1.0, rho=rho)
+    s = mo.zero_state(p)
+    for k in range(1, 9):
+        s = mo.iterate(p, s, 1)
+        want = np.where(y > 0, y * (1.0 - (1.0 - rho * tau) ** k), 0.0)
+        assert np.max(np.abs(s.X - want)) < 1e-14
+        assert not s.U.any() and not s.V.any()
+
+
 def test_condat_step_sizes():
     tau, sigma, rho, delta = mo.condat_steps(2.0, 5.0, sigma=1.0)
     assert 1.0 / tau - sigma * 5.0 > 1.0 and 1.0 <= delta < 2.0 and rho == 1.0
@@ -411,7 +478,7 @@ def test_successive_differences_shrink_in_condat_metric_union():
 
 # ---------------------------------------------------------------- the pins catch planted mistakes
 
-@pytest.mark.parametrize("plant", ["grad_sign", "dilation", "dct_transpose", "adjoint_gen", "relax"])
+@pytest.mark.parametrize("plant", ["grad_sign", "dilation", "dct_transpose", "adjoint_gen", "relax", "relax_rho"])
 def test_planted_mistakes_are_caught(plant, monkeypatch):
     """Plant a plausible bug in the oracle (CPU) and check a pin above fails."""
     if plant == "grad_sign":
@@ -450,3 +517,22 @@ def test_planted_mistakes_are_caught(plant, monkeypatch):
         monkeypatch.setattr(mo, "iterate", wrong)
         with pytest.raises(AssertionError):
             test_successive_differences_shrink_in_condat_metric(1)
+    elif plant == "relax_rho":
+        def swapped(p, s, n_iter=1):   # rho and 1 - rho exchanged in the three relaxation lines
+            X, U, V = s.X, s.U, s.V
+            for _ in range(n_iter):
+                Xt = mo.positive(X - p.tau * (mo.gradient(X, p.y, p.hhat, p.w)
+                                              + p.mu_s * mo.ws_adjoint(p, U)
+                                              + p.mu_l * mo.spectral_adjoint(V)))
+                Ut = mo.sat(U + p.sigma * p.mu_s * mo.ws_analysis(p, 2.0 * Xt - X))
+                Vt = mo.sat(V + p.sigma * p.mu_l * mo.spectral_analysis(2.0 * Xt - X))
+                X = (1.0 - p.rho) * Xt + p.rho * X
+                U = (1.0 - p.rho) * Ut + p.rho * U
+                V = (1.0 - p.rho) * Vt + p.rho * V
+            return mo.State(X, U, V, s.it + n_iter)
+        monkeypatch.setattr(mo, "iterate", swapped)
+        with pytest.raises((AssertionError, FloatingPointError)):
+            with np.errstate(all="ignore"):
+                test_relaxed_iteration_reaches_independent_minimiser("gen1_J1", 1.5)
+        with pytest.raises(AssertionError):
+            test_relaxed_primal_trajectory_closed_form(0.6)
