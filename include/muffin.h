@@ -50,7 +50,7 @@ typedef enum {
   MUFFIN_ERR_NOMEM = -3,      /* workspace too small */
   MUFFIN_ERR_STATE = -4,      /* call out of order */
   MUFFIN_ERR_NONFINITE = -5,  /* NaN or Inf in an input or in the state */
-  MUFFIN_ERR_TIMEOUT = -6     /* reserved: a bounded device wait gave up */
+  MUFFIN_ERR_TIMEOUT = -6     /* a bounded device wait gave up (network calls: muffin_net.h) */
 } muffin_status;
 
 /* Parameters of Eqs. 5-6 and Algorithm 1. */

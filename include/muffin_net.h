@@ -76,7 +76,9 @@ int muffin_net_get_params(const muffin_net* net, float* d_theta);
 /* Prediction of the starting state from the dirty cube d_dirty (float32
  * [nz][ny][nx], device): d_x = max(s * z[0], 0) (float32 [nz][ny][nx]) and,
  * if n_out > 1, d_aux = clamp(z[k], -1, 1) (float32 [nz][n_out-1][ny][nx];
- * may be NULL only when n_out == 1).  Asynchronous. */
+ * may be NULL only when n_out == 1).  Synchronises the stream and returns
+ * MUFFIN_ERR_TIMEOUT when a tensor-core wait gave up (the prediction is then
+ * incomplete and must not be used); see muffin_net_check. */
 int muffin_net_predict(muffin_net* net, const float* d_dirty, float* d_x, float* d_aux);
 
 /* Loss at (d_dirty, d_target_x, d_target_aux) and its packed gradient
@@ -90,11 +92,31 @@ int muffin_net_loss_grad(muffin_net* net, const float* d_dirty, const float* d_t
 
 /* One Adam step on the pair at learning rate lr (finite, >= 0).  Training
  * contexts only.  d_loss (device, may be NULL) receives the loss of the pair
- * before the step, as a double.  Asynchronous. */
+ * before the step, as a double.  Asynchronous: if a tensor-core wait of this
+ * step (or of an unchecked earlier call on the device) gave up, the device
+ * drops the parameter update instead of applying an incomplete gradient, and
+ * the next muffin_net_check reports MUFFIN_ERR_TIMEOUT. */
 int muffin_net_train_step(muffin_net* net, const float* d_dirty, const float* d_target_x,
                           const void* d_target_aux, float lr, double* d_loss);
 
 const char* muffin_net_last_error(const muffin_net* net);  /* net may be NULL (create errors) */
+
+/* Wait for the context's stream, then read and clear the device's count of
+ * tensor-core waits that gave up (a wait that runs out of polls makes its
+ * thread block record the give-up, drain its copies and MMAs in flight at the
+ * full bound, skip its remaining tiles and free its tensor memory; the GPU
+ * context stays usable).  Returns
+ * MUFFIN_OK, or MUFFIN_ERR_TIMEOUT when the count was not zero (described by
+ * muffin_net_last_error).  The count is per device, shared by all network
+ * contexts and single-layer calls on it. */
+int muffin_net_check(muffin_net* net);
+
+/* Poll bound of the tensor-core pipeline waits on the current device (each
+ * poll is one mbarrier try_wait, which may suspend for a bounded time);
+ * polls < 0 restores the default 2^20.  0 makes every pipeline wait give up
+ * at once (used by the tests of the give-up path).  Returns MUFFIN_OK or
+ * MUFFIN_ERR_CUDA.  Takes effect for kernels launched afterwards. */
+int muffin_net_set_wait_limit(long long polls);
 
 /* Number of tensor-core waits of the 32 -> 32 layers on the current device
  * that gave up since the last call (a layer whose wait gives up leaves its

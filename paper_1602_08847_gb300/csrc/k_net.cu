@@ -229,6 +229,10 @@ __host__ __device__ constexpr uint32_t idesc_bf16(int no) {
 constexpr long long kWaitLimit = 1LL << 20;   // polls; each may suspend for a bounded time
 
 __device__ int g_tc_timeouts;
+// Poll bound of the pipeline waits (settable through muffin_net_set_wait_limit).
+// The drain waits after a give-up keep the full bound kWaitLimit, so that no
+// copy or MMA lands in shared or tensor memory after the CTA has left.
+__device__ long long g_wait_polls = kWaitLimit;
 
 struct HaloMaps {
   CUtensorMap m[4];   // one per 8-feature chunk
@@ -245,9 +249,9 @@ __device__ __forceinline__ uint64_t umma_desc(uint32_t addr, uint32_t lbo, uint3
 __device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
 __device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
 
-__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
+__device__ __forceinline__ bool mbar_wait_n(uint32_t bar, uint32_t parity, long long limit) {
   uint32_t done = 0;
-  for (long long it = 0; it < kWaitLimit && !done; ++it) {
+  for (long long it = 0; it < limit && !done; ++it) {
     asm volatile(
         "{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\nselp.u32 %0, 1, 0, p;\n}\n"
         : "=r"(done)
@@ -256,6 +260,12 @@ __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
   }
   return done != 0;
 }
+// pipeline wait: gives up after g_wait_polls polls
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
+  return mbar_wait_n(bar, parity, *(volatile long long*)&g_wait_polls);
+}
+// drain wait after a give-up: the full bound
+__device__ __forceinline__ bool mbar_drain(uint32_t bar, uint32_t parity) { return mbar_wait_n(bar, parity, kWaitLimit); }
 
 // Thread 0: the four chunk boxes of the tile at (x0, y0, z0) into halo buffer s_dst.
 __device__ __forceinline__ void issue_halo(const HaloMaps& maps, uint32_t s_dst, uint32_t bar, int x0, int y0,
@@ -332,6 +342,9 @@ k_conv_tc05(const __grid_constant__ HaloMaps maps, const bf16* __restrict__ wk, 
   // exit can wait for it before the CTA's shared memory goes away
   bool pending = false;
   uint32_t pend_ph = 0;
+  // and the MMAs it committed but has not yet seen finish
+  bool mma_pending = false;
+  uint32_t mma_ph = 0;
   if (threadIdx.x == 0 && (int)blockIdx.x < ntiles) {
     int x0, y0, z0;
     origin(blockIdx.x, x0, y0, z0);
@@ -369,9 +382,12 @@ k_conv_tc05(const __grid_constant__ HaloMaps maps, const bf16* __restrict__ wk, 
         }
         asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(s_done)
                      : "memory");
+        mma_pending = true;
+        mma_ph = ph;
       }
     }
     const bool done = mbar_wait(s_done, ph);
+    if (threadIdx.x == 0 && done) mma_pending = false;
     if (__syncthreads_or(!done)) {          // one decision for the whole block
       if (threadIdx.x == 0) atomicAdd(&g_tc_timeouts, 1);
       break;
@@ -463,7 +479,9 @@ k_conv_tc05(const __grid_constant__ HaloMaps maps, const bf16* __restrict__ wk, 
     __syncthreads();     // the accumulator is read before the next tile's MMAs overwrite it
     tc_fence_after();
   }
-  if (threadIdx.x == 0 && pending) mbar_wait(s_full, pend_ph);   // only after a timeout
+  // only after a give-up: the copy and the MMAs still in flight land before the CTA leaves
+  if (threadIdx.x == 0 && pending) mbar_drain(s_full, pend_ph);
+  if (threadIdx.x == 0 && mma_pending) mbar_drain(s_done, mma_ph);
   tc_fence_before();
   __syncthreads();
   tc_fence_after();
@@ -628,7 +646,7 @@ k_wgrad_tc05(const __grid_constant__ WgradMaps maps, float* __restrict__ part, f
     asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(s_fin) : "memory");
     if (!ok)
       for (int b = 0; b < WG_NS; ++b)
-        if ((used >> b) & 1u) mbar_wait(s_full + 8 * b, ((odd >> b) & 1u) ^ 1u);
+        if ((used >> b) & 1u) mbar_drain(s_full + 8 * b, ((odd >> b) & 1u) ^ 1u);
   } else if (warp == 1) {
     // bias gradient: bacc = sum of dz[p][co = lane] over this CTA's voxels
     for (int it = 0; it < nmine && ok; ++it) {
@@ -643,7 +661,7 @@ k_wgrad_tc05(const __grid_constant__ WgradMaps maps, float* __restrict__ part, f
       asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(s_freed + 8 * s) : "memory");
     }
   }
-  const bool fin = mbar_wait(s_fin, 0);
+  const bool fin = mbar_drain(s_fin, 0);   // every MMA issued, also after a give-up: TMEM is freed below
   if (__syncthreads_or(!ok || !fin)) {
     if (threadIdx.x == 0) atomicAdd(&g_tc_timeouts, 1);
   } else {
@@ -1044,6 +1062,9 @@ __global__ void k_adam(float* __restrict__ theta, const float* __restrict__ g, f
                        float* __restrict__ v, int n, float lr, float c1, float c2) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
+  // a layer of this step (or an unchecked earlier call) gave up a wait: its
+  // gradient is incomplete, so the step is dropped; muffin_net_check reports it
+  if (*(volatile int*)&g_tc_timeouts != 0) return;
   const float gi = g[i];
   const float mi = 0.9f * m[i] + 0.1f * gi;
   const float vi = 0.999f * v[i] + 0.001f * gi * gi;
@@ -1514,13 +1535,43 @@ int muffin_net_get_params(const muffin_net* n, float* d_theta) {
   return cuda_check(const_cast<muffin_net*>(n), "muffin_net_get_params");
 }
 
+// Synchronise the context's stream, then read and clear the device's count of
+// tensor-core waits that gave up; MUFFIN_ERR_TIMEOUT if it was not zero.
+static int check_waits(muffin_net* n, const char* what) {
+  cudaError_t e = cudaStreamSynchronize(n->st);
+  if (e != cudaSuccess) return fail(n, MUFFIN_ERR_CUDA, std::string(what) + ": " + cudaGetErrorString(e));
+  int v = 0, zero = 0;
+  if ((e = cudaMemcpyFromSymbol(&v, g_tc_timeouts, sizeof(int))) != cudaSuccess ||
+      (e = cudaMemcpyToSymbol(g_tc_timeouts, &zero, sizeof(int))) != cudaSuccess)
+    return fail(n, MUFFIN_ERR_CUDA, std::string(what) + ": " + cudaGetErrorString(e));
+  if (v != 0)
+    return fail(n, MUFFIN_ERR_TIMEOUT, std::string(what) + ": " + std::to_string(v) +
+                                           " thread block(s) of the tensor-core layers gave up a bounded wait; "
+                                           "their output tiles (and any Adam step queued after them) were skipped");
+  return MUFFIN_OK;
+}
+
 int muffin_net_predict(muffin_net* n, const float* d_dirty, float* d_x, float* d_aux) {
   if (!n) return MUFFIN_ERR_ARG;
   if (!d_dirty || !d_x) return fail(n, MUFFIN_ERR_ARG, "NULL cube pointer");
   if (n->K > 1 && !d_aux) return fail(n, MUFFIN_ERR_ARG, "NULL d_aux with more than one output map");
   forward_to_a5(n, d_dirty);
   last_predict(n, d_x, d_aux);
-  return cuda_check(n, "muffin_net_predict");
+  const int r = cuda_check(n, "muffin_net_predict");
+  if (r != MUFFIN_OK) return r;
+  return check_waits(n, "muffin_net_predict");
+}
+
+int muffin_net_check(muffin_net* n) {
+  if (!n) return MUFFIN_ERR_ARG;
+  const int r = cuda_check(n, "muffin_net_check");
+  if (r != MUFFIN_OK) return r;
+  return check_waits(n, "muffin_net_check");
+}
+
+int muffin_net_set_wait_limit(long long polls) {
+  const long long v = polls < 0 ? kWaitLimit : polls;
+  return cudaMemcpyToSymbol(g_wait_polls, &v, sizeof(v)) == cudaSuccess ? MUFFIN_OK : MUFFIN_ERR_CUDA;
 }
 
 static int check_targets(muffin_net* n, const float* d_dirty, const float* d_tx, const void* d_taux) {
@@ -1542,8 +1593,7 @@ int muffin_net_loss_grad(muffin_net* n, const float* d_dirty, const float* d_tx,
   if (r != MUFFIN_OK) return r;
   if (h_loss) {
     cudaMemcpyAsync(h_loss, n->loss, 8, cudaMemcpyDeviceToHost, n->st);
-    const cudaError_t e = cudaStreamSynchronize(n->st);
-    if (e != cudaSuccess) return fail(n, MUFFIN_ERR_CUDA, std::string("muffin_net_loss_grad: ") + cudaGetErrorString(e));
+    return check_waits(n, "muffin_net_loss_grad");
   }
   return MUFFIN_OK;
 }

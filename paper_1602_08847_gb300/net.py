@@ -27,6 +27,8 @@ _SIG = {
     "muffin_net_train_step": (_I, [_P, _P, _P, _P, _F, _P]),
     "muffin_net_last_error": (ctypes.c_char_p, [_P]),
     "muffin_net_wait_timeouts": (_I, []),
+    "muffin_net_check": (_I, [_P]),
+    "muffin_net_set_wait_limit": (_I, [ctypes.c_longlong]),
     "muffin_net_destroy": (None, [_P]),
     "muffin_conv3d_scratch_bytes": (_S, [_I, _I, _I]),
     "muffin_conv3d_forward": (_I, [_P, _P, _P, _I, _P, _I, _I, _I, _P, _S, _P]),
@@ -56,6 +58,13 @@ N_PARAMS = n_params(1)
 def wait_timeouts() -> int:
     """Tensor-core waits that gave up since the last call (0 in a healthy run)."""
     return int(_lib.muffin_net_wait_timeouts())
+
+
+def set_wait_limit(polls: int | None) -> None:
+    """Poll bound of the tensor-core pipeline waits (None: the default 2^20)."""
+    r = int(_lib.muffin_net_set_wait_limit(-1 if polls is None else int(polls)))
+    if r != 0:
+        raise _m.MuffinError(r, "muffin_net_set_wait_limit failed")
 
 
 def _ptr(t):
@@ -167,6 +176,11 @@ class WarmStartNet:
             raise ValueError("loss_out must be a float64 CUDA tensor")
         self._check(_lib.muffin_net_train_step(self._net, dirty.data_ptr(), target_x.data_ptr(), _ptr(ta),
                                                float(lr), _ptr(loss_out)))
+
+    def check(self):
+        """Wait for the stream; raise MuffinError(TIMEOUT) if a tensor-core wait gave up
+        since the last check (the parameter updates queued after it were dropped)."""
+        self._check(_lib.muffin_net_check(self._net))
 
     def close(self):
         if getattr(self, "_net", None) is not None and self._net.value:

@@ -77,7 +77,11 @@ def make_pairs(cfg: str, seeds, iters: int, workers: int, fine_levels: int = -1,
 def train(net: WarmStartNet, dirty, target_x, target_u, epochs: int, lr: float, lr_final: float, seed: int = 0,
           log_every: int = 100) -> list[float]:
     """Adam over the pairs in a seeded random order, learning rate cosine-decayed
-    from lr to lr_final; returns the mean loss of every log_every steps."""
+    from lr to lr_final; returns the mean loss of every log_every steps.
+
+    Every log_every steps (and at the end) the network's bounded tensor-core
+    waits are checked: a wait that gave up raises MuffinError(TIMEOUT) and
+    stops the training (the device already dropped the updates after it)."""
     rng = np.random.Generator(np.random.PCG64(seed))
     n = len(dirty)
     total = epochs * n
@@ -88,6 +92,9 @@ def train(net: WarmStartNet, dirty, target_x, target_u, epochs: int, lr: float, 
             r = lr_final + 0.5 * (lr - lr_final) * (1.0 + np.cos(np.pi * step / max(total - 1, 1)))
             net.train_step(dirty[i], target_x[i], target_u[i] if net.n_out > 1 else None, r, loss[step:step + 1])
             step += 1
+            if step % log_every == 0:
+                net.check()
+    net.check()
     curve = loss.cpu().numpy()
     return [float(curve[k:k + log_every].mean()) for k in range(0, total, log_every)]
 

@@ -24,3 +24,16 @@ def lib():
         pytest.skip("no CUDA device")
     from paper_1602_08847_gb300 import muffin
     return muffin
+
+
+def pytest_collection_finish(session):
+    """When the precision tests are selected on a machine with a GPU, start their
+    long FP64 oracle runs now (in spawned worker processes, before any CUDA call
+    of this process) so that they overlap the other GPU tests."""
+    if not any("test_gpu_precision" in item.nodeid for item in session.items):
+        return
+    import torch
+    if not torch.cuda.is_available():
+        return
+    import oracle_jobs
+    oracle_jobs.start()

@@ -12,13 +12,14 @@ import torch
 from oracle import muffin_oracle as mo
 from paper_1602_08847_gb300 import synth
 from gpu_helpers import max_rel
+import oracle_jobs as oj
 
 pytestmark = pytest.mark.gpu
 TOL1 = 2e-5
 
 
 def _setup(name):
-    cube = synth.make_cube(name)
+    cube = oj.cube(name)      # generated once per session (shared with the precision tests)
     cfg = cube.cfg
     L, n, J = cfg.nchan, cfg.n, cfg.nscales
     hh = mo.psf_multiplier(cube.psf)

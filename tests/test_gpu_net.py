@@ -253,6 +253,46 @@ def test_network_argument_errors(netmod):
         n.loss_grad(torch.zeros((2, 8, 8), device="cuda"), torch.zeros((2, 8, 8), device="cuda"))
 
 
+def test_wait_give_up_is_reported_and_context_survives(netmod):
+    """Failure detection of the bounded tensor-core waits, without a GPU fault:
+    with the poll bound at 0 every pipeline wait gives up at once; each thread
+    block drains its copy and MMAs in flight (full bound), frees its tensor
+    memory and returns.  The prediction reports MUFFIN_ERR_TIMEOUT, the Adam
+    step queued after a timed-out gradient is dropped on the device and
+    reported by check(); with the bound restored the same context gives the
+    prediction of an untouched run, bit for bit, and trains again."""
+    from paper_1602_08847_gb300.muffin import MuffinError
+    shape, K = (6, 40, 24), 3
+    theta = torch.from_numpy(synth.net_init(21, K).astype(np.float32)).cuda()
+    y = torch.from_numpy(synth.random_field(shape, 22, -0.3, 1.0).astype(np.float32)).cuda()
+    ref = netmod.WarmStartNet(shape, theta=theta, n_out=K)
+    x_ref, aux_ref = ref.predict(y)
+    ref.close()
+    n = netmod.WarmStartNet(shape, theta=theta, n_out=K)
+    tr = netmod.WarmStartNet(shape, training=True, theta=theta, n_out=K)
+    tx = torch.relu(y)
+    ta = torch.zeros((shape[0], K - 1, shape[1], shape[2]), dtype=torch.bfloat16, device="cuda")
+    try:
+        netmod.set_wait_limit(0)
+        with pytest.raises(MuffinError, match="TIMEOUT"):
+            n.predict(y)
+        before = tr.get_params().clone()
+        tr.train_step(y, tx, ta, 1e-2)
+        with pytest.raises(MuffinError, match="TIMEOUT"):
+            tr.check()
+        assert torch.equal(tr.get_params(), before)      # the update was dropped
+    finally:
+        netmod.set_wait_limit(None)
+    x, aux = n.predict(y)
+    assert torch.equal(x, x_ref) and torch.equal(aux, aux_ref)
+    tr.train_step(y, tx, ta, 1e-2)
+    tr.check()
+    assert not torch.equal(tr.get_params(), before)
+    n.close()
+    tr.close()
+    assert netmod.wait_timeouts() == 0
+
+
 def test_no_tensor_core_wait_gave_up(netmod):
     """Every bounded wait of the tcgen05 layers above ended by completion."""
     assert netmod.wait_timeouts() == 0
