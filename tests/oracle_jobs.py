@@ -60,18 +60,27 @@ CUBE_64x64x256 = synth.CubeConfig("64x64x256", n=64, nchan=256, n_src=40, n_ant=
 BATCH = ("128x128x16", "256x256x32", "512x512x64", "1024x1024x8")
 
 
+# Two cases take the oracle many minutes: the full 256 x 256 x 64 cube with
+# every term (all channels coupled, so one process: about 7 minutes for 100
+# passes on one host core) and the union of bases on it (the oracle's DWT
+# matrices: about 15 minutes of host time in 8 slices).  They run when
+# MUFFIN_PRECISION_FULL is set; the other cases always run.
+FULL = bool(os.environ.get("MUFFIN_PRECISION_FULL"))
+
+
 def _plan():
     """case -> dict(cube, J, gen, mu_l, dictionary, groups): groups are channel lists, one job each."""
     plan = {
-        "256x256x64": dict(cube="256x256x64", J=4, mu_l=MU_L, dictionary="iuwt", groups=[None]),
         "64x64x256": dict(cube=CUBE_64x64x256, J=3, mu_l=MU_L, dictionary="iuwt", groups=[None]),
         "512x512x256_mu_l0": dict(cube="512x512x256", J=5, mu_l=0.0, dictionary="iuwt", groups=[[0], [128], [255]]),
-        "union_256x256x64_mu_l0": dict(cube="256x256x64", J=4, mu_l=0.0, dictionary="union",
-                                       groups=[list(range(8 * k, 8 * k + 8)) for k in range(8)]),
     }
     for name in BATCH:
         L = synth.CONFIGS[name].nchan
         plan["batch_" + name] = dict(cube=name, J=4, mu_l=0.0, dictionary="iuwt", groups=[[0], [L - 1]])
+    if FULL:
+        plan["256x256x64"] = dict(cube="256x256x64", J=4, mu_l=MU_L, dictionary="iuwt", groups=[None])
+        plan["union_256x256x64_mu_l0"] = dict(cube="256x256x64", J=4, mu_l=0.0, dictionary="union",
+                                              groups=[list(range(8 * k, 8 * k + 8)) for k in range(8)])
     return plan
 
 
@@ -84,7 +93,8 @@ def start():
     for k in env_keep:
         os.environ[k] = "1"           # one thread per worker: the workers share the host's cores
     try:
-        _pool = cf.ProcessPoolExecutor(max_workers=max(2, min(16, (os.cpu_count() or 2) - 1)),
+        # half the host's cores: the GPU tests of this process run their own oracle checks meanwhile
+        _pool = cf.ProcessPoolExecutor(max_workers=max(2, min(8, (os.cpu_count() or 4) // 2)),
                                        mp_context=mp.get_context("spawn"))
     finally:
         for k, v in env_keep.items():
