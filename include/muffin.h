@@ -50,7 +50,7 @@ typedef enum {
   MUFFIN_ERR_NOMEM = -3,      /* workspace too small */
   MUFFIN_ERR_STATE = -4,      /* call out of order */
   MUFFIN_ERR_NONFINITE = -5,  /* NaN or Inf in an input or in the state */
-  MUFFIN_ERR_TIMEOUT = -6     /* a bounded device wait gave up (network calls: muffin_net.h) */
+  MUFFIN_ERR_TIMEOUT = -6     /* a bounded device wait gave up (muffin_objective, network calls) */
 } muffin_status;
 
 /* Parameters of Eqs. 5-6 and Algorithm 1. */
@@ -99,7 +99,11 @@ int muffin_iterate(muffin_ctx* ctx, int n_iter);
 
 /* Objective of Eqs. 5-6 at the current X (positivity holds by construction):
  * h_obj[0] = total; if h_terms != NULL it receives (data term, mu_s spatial
- * l1, mu_lambda spectral l1).  FP64 FFT and FP64 reductions.  Synchronises. */
+ * l1, mu_lambda spectral l1).  FP64 FFT and FP64 reductions.  Synchronises.
+ * Returns MUFFIN_ERR_TIMEOUT if, since the last check, a thread block of a
+ * pipelined (TMA) pass kernel -- the spectral step or the column filter --
+ * gave up one of its bounded waits (its tiles were then not written; the
+ * count is per device). */
 int muffin_objective(muffin_ctx* ctx, double* h_obj, double* h_terms);
 
 /* Current X out to / in from a device cube [L][N][N] (warm start: set X and
@@ -138,6 +142,18 @@ const char* muffin_stage_name(int k);
 double muffin_stage_bytes(const muffin_ctx* ctx, int k);
 /* Number of kernels one pass of Algorithm 1 launches for this context. */
 int muffin_kernels_per_iteration(const muffin_ctx* ctx);
+/* Schedule of one pass (no change to what it computes): the gradient FFTs,
+ * the primal step and the spatial analysis and adjoint run per group of
+ * channels_per_group channels (0: the whole cube as one group), so that the
+ * row spectra and the c_j1 / r_j1 hand-offs of a group stay in the L2 cache;
+ * groups alternate between `branches` (1..3) concurrent branches of the
+ * pass's CUDA graph, and the spectral step runs on its own branch once every
+ * group's D is written.  Results are bitwise the same for every plan.
+ * muffin_plan reports the plan in effect (groups never exceed the channel
+ * count; branches never exceed the group count). */
+int muffin_set_plan(muffin_ctx* ctx, int channels_per_group, int branches);
+int muffin_plan(const muffin_ctx* ctx, int* channels_per_group, int* branches);
+
 /* Wavelet tiling in use: levels j < *fine_levels run on halo tiles, the others
  * on class sub-images split over *cluster blocks (0: single-block streaming
  * kernel).  Either pointer may be NULL. */

@@ -15,12 +15,16 @@ struct Geom {
   int j1;       // fine levels computed on halo tiles; levels >= j1 run class-permuted
   int cs;       // blocks per cluster of the coarse kernel (0: single-block streaming kernel)
   int dict = 0; // W_s: 0 IUWT, 1 union of eight Daubechies bases (k_dwt.cu)
+  int vec = 1;  // generation 1: the vectorised pass kernels (k_iuwt_vec.cu) where the geometry allows
 };
 
 // ---- FFT path (k_fft.cu) ----
 // Per-channel H_l^T H_l x_l (weights and 1/N^2 folded into Kp, Kb) followed
 // by the primal step of Algorithm 1, or, in power mode, only H^T H x -> out.
 cudaError_t launch_rows_fwd(const float* X, float* spec, int n, int L, const float* twf, cudaStream_t s);
+// Blocks of the pipelined column filter that gave up a bounded wait since the
+// last call (resets the count); -1 on a CUDA error.
+int fft_take_timeouts();
 cudaError_t launch_cols_filter(float* spec, const float* Kp, const float* Kb, int n, int L, const float* twf,
                                cudaStream_t s);
 struct PrimalArgs {
@@ -71,6 +75,15 @@ cudaError_t launch_coarse(const Geom& g, const float* c_in, float* r_out, float*
                           double* partials, cudaStream_t s, int* nblocks);
 // Opt the wavelet kernels into shared memory and pick g.cs for this device.
 cudaError_t iuwt_configure(Geom& g);
+// Vectorised generation-1 kernels of the pass (k_iuwt_vec.cu): 64 x 64 fine
+// tiles with j1 in 1..3, coarse sub-images of 32 or 64 with 1..3 levels.
+bool iuwt_vec_fine_ok(const Geom& g);
+bool iuwt_vec_coarse_ok(const Geom& g);
+cudaError_t launch_fine_analysis_vec(const Geom& g, const IuwtArgs& a, cudaStream_t s);
+cudaError_t launch_fine_adjoint_vec(const Geom& g, const IuwtArgs& a, cudaStream_t s);
+cudaError_t launch_coarse_vec(const Geom& g, const float* c_in, float* r_out, float* U, float k, float rho,
+                              cudaStream_t s);
+cudaError_t iuwt_vec_configure();
 cudaError_t fft_configure(int n);
 
 // ---- W_s as a union of eight orthonormal Daubechies bases (k_dwt.cu) ----
@@ -113,6 +126,9 @@ struct SpecArgs {
 };
 bool spectral_uses_fft(int L);
 cudaError_t spectral_configure(int L);
+// Blocks of the pipelined spectral kernel that gave up a bounded wait since the
+// last call (resets the count); -1 on a CUDA error.  Synchronises the device.
+int spectral_take_timeouts();
 cudaError_t launch_spectral(const SpecArgs& a, int npix, int L, int mode, cudaStream_t s, int* nblocks);
 
 // ---- misc (k_misc.cu) ----

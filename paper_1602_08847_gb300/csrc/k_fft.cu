@@ -13,6 +13,9 @@
 //                   update of Algorithm 1 (second line; Eq. 10) in the
 //                   epilogue: X~ = (X - tau (grad + mu_s S + mu_l T))_+,
 //                   D = 2 X~ - X, X <- rho X~ + (1 - rho) X.
+#include <cuda.h>   // CUtensorMap (the encoder is reached through the runtime's driver entry point)
+#include <cstdlib>
+
 #include "device.cuh"
 #include "internal.h"
 
@@ -103,6 +106,195 @@ k_cols_filter(cpx<float>* __restrict__ spec, const float* __restrict__ Kp, const
   fft_regs<float, N, 1, C>(v, buf + c, tw, t);
 #pragma unroll
   for (int q = 0; q < 8; ++q) base[(t + q * T8) * H + kx] = v[q];
+}
+
+// ------------------------------------------------------------------ column filter, pipelined (TMA)
+// The column filter above as a persistent kernel: a block walks strips of C
+// spectrum columns of one channel; the strip ([N][C] complex) and its
+// multipliers ([N][C] floats) arrive by 2-D TMA copies into a double buffer,
+// so the next strip's loads run under this strip's two FFTs, and the filtered
+// strip leaves by TMA stores from the same buffer.  Bounded mbarrier waits: a
+// block that gives up records it in g_fft_timeouts, waits (bounded) for its
+// copies in flight and returns.
+__device__ int g_fft_timeouts;
+constexpr long long kFftPolls = 1LL << 22;
+
+struct ColMaps {
+  CUtensorMap spec;   // [L N rows][N floats], box [BR][2C]
+  CUtensorMap k;      // [L N rows][N/2 floats], box [BR][C]
+};
+
+template <int N> __host__ __device__ constexpr int colt_c() { return N >= 512 ? 8 : 16; }
+template <int N> __host__ __device__ constexpr int colt_br() { return N < 256 ? N : 256; }
+template <int N> struct ColTma {
+  static constexpr int C = colt_c<N>(), BR = colt_br<N>();
+  static constexpr size_t SPEC = (size_t)N * C * sizeof(cpx<float>), KB = (size_t)N * C * sizeof(float);
+  static constexpr size_t OFF_S = 0, OFF_K = 2 * SPEC, OFF_TW = OFF_K + 2 * KB;
+  static constexpr size_t OFF_BAR = OFF_TW + (size_t)N * sizeof(cpx<float>);
+  static constexpr size_t SMEM = OFF_BAR + 64 + 128;
+};
+
+template <int N>
+__global__ void __launch_bounds__(colt_c<N>() * (N / 8), 1)
+k_cols_tma(const __grid_constant__ ColMaps maps, const float* __restrict__ Kb, const cpx<float>* __restrict__ twg,
+           int ntiles) {
+  using G = ColTma<N>;
+  constexpr int T8 = N / 8, C = G::C, BR = G::BR, H = N / 2, STRIPS = H / C;
+  extern __shared__ __align__(16) unsigned char smraw[];
+  unsigned char* sm = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smraw) + 127) & ~(uintptr_t)127);
+  cpx<float>* Sb = reinterpret_cast<cpx<float>*>(sm + G::OFF_S);
+  float* Kbuf = reinterpret_cast<float*>(sm + G::OFF_K);
+  cpx<float>* tw = reinterpret_cast<cpx<float>*>(sm + G::OFF_TW);
+  const uint32_t bar0 = smem_addr(sm + G::OFF_BAR);
+  const int tid = threadIdx.x, c = tid % C, t = tid / C;
+  for (int i = tid; i < N; i += blockDim.x) tw[i] = twg[i];
+  constexpr uint32_t kBytes = (uint32_t)(G::SPEC + G::KB);
+  auto issue = [&](int tile, int s) {
+    const int l = tile / STRIPS, strip = tile % STRIPS;
+    const uint32_t bar = bar0 + 8 * s;
+    mbar_expect(bar, kBytes);
+#pragma unroll
+    for (int r = 0; r < N / BR; ++r) {
+      tma_load2(smem_addr(Sb + (size_t)s * N * C + (size_t)r * BR * C), &maps.spec, 2 * strip * C, l * N + r * BR, bar);
+      tma_load2(smem_addr(Kbuf + (size_t)s * N * C + (size_t)r * BR * C), &maps.k, strip * C, l * N + r * BR, bar);
+    }
+  };
+  uint32_t pend = 0, pend_ph = 0;   // thread 0: stages with a load in flight, and its phase parity
+  if (tid == 0) {
+    mbar_init(bar0, 1);
+    mbar_init(bar0 + 8, 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    for (int b = 0; b < 2; ++b)
+      if ((int)blockIdx.x + b * (int)gridDim.x < ntiles) {
+        issue(blockIdx.x + b * gridDim.x, b);
+        pend |= 1u << b;
+      }
+  }
+  __syncthreads();
+  bool gave_up = false;
+  int it = 0;
+  for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x, ++it) {
+    const int s = it & 1;
+    const uint32_t ph = (uint32_t)(it >> 1) & 1u;
+    const bool ok = mbar_try(bar0 + 8 * s, ph, kFftPolls);
+    if (__syncthreads_or(!ok)) { gave_up = true; break; }
+    if (tid == 0) pend &= ~(1u << s);
+    const int l = tile / STRIPS, strip = tile % STRIPS;
+    const int kx = strip * C + c;
+    cpx<float>* buf = Sb + (size_t)s * N * C;
+    const float* Kt = Kbuf + (size_t)s * N * C;
+    cpx<float> v[8];
+    float ka[8], kb[8];
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+      v[q] = buf[(t + q * T8) * C + c];
+      ka[q] = Kt[(t + q * T8) * C + c];
+      kb[q] = kx == 0 ? __ldg(Kb + (size_t)l * N + t + q * T8) : 0.0f;
+    }
+    fft_regs<float, N, -1, C>(v, buf + c, tw, t);
+    __syncthreads();
+#pragma unroll
+    for (int q = 0; q < 8; ++q) buf[(t + q * T8) * C + c] = v[q];
+    __syncthreads();
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+      const int pos = t + q * T8;
+      if (kx == 0) {
+        const cpx<float> zm = buf[((N - pos) & (N - 1)) * C + c];
+        v[q] = add(scale(v[q], ka[q]), scale(conj(zm), kb[q]));
+      } else {
+        v[q] = scale(v[q], ka[q]);
+      }
+    }
+    fft_regs<float, N, 1, C>(v, buf + c, tw, t);
+    __syncthreads();
+#pragma unroll
+    for (int q = 0; q < 8; ++q) buf[(t + q * T8) * C + c] = v[q];
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    __syncthreads();
+    if (tid == 0) {
+#pragma unroll
+      for (int r = 0; r < N / BR; ++r)
+        tma_store2(&maps.spec, 2 * strip * C, l * N + r * BR, smem_addr(buf + (size_t)r * BR * C));
+      asm volatile("cp.async.bulk.commit_group;" ::: "memory");
+      const int next = tile + 2 * gridDim.x;
+      if (next < ntiles) {
+        asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory");
+        issue(next, s);
+        pend |= 1u << s;
+        pend_ph = (pend_ph & ~(1u << s)) | ((((uint32_t)(it >> 1) + 1u) & 1u) << s);
+      }
+    }
+  }
+  if (tid == 0) {
+    if (gave_up) {
+      atomicAdd(&g_fft_timeouts, 1);
+      for (int b = 0; b < 2; ++b)
+        if ((pend >> b) & 1u) mbar_try(bar0 + 8 * b, (pend_ph >> b) & 1u, kFftPolls);
+    }
+    asm volatile("cp.async.bulk.wait_group 0;" ::: "memory");
+  }
+}
+
+typedef CUresult (*FftEncodeFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+static FftEncodeFn fft_encoder() {
+  static FftEncodeFn fn = nullptr;
+  static bool tried = false;
+  if (!tried) {
+    tried = true;
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<FftEncodeFn>(p);
+  }
+  return fn;
+}
+
+// 2-D float32 map: rows x width floats (row pitch = width), box bh x bw.
+static bool fft_map(CUtensorMap* m, const float* base, size_t rows, size_t width, int bw, int bh) {
+  FftEncodeFn enc = fft_encoder();
+  if (!enc) return false;
+  const cuuint64_t dims[2] = {(cuuint64_t)width, (cuuint64_t)rows};
+  const cuuint64_t strides[1] = {(cuuint64_t)width * sizeof(float)};
+  const cuuint32_t box[2] = {(cuuint32_t)bw, (cuuint32_t)bh};
+  const cuuint32_t estr[2] = {1, 1};
+  return enc(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<float*>(base), dims, strides, box, estr,
+             CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+             CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+int fft_take_timeouts() {
+  int v = 0, zero = 0;
+  if (cudaMemcpyFromSymbol(&v, g_fft_timeouts, sizeof(int)) != cudaSuccess) return -1;
+  if (v != 0 && cudaMemcpyToSymbol(g_fft_timeouts, &zero, sizeof(int)) != cudaSuccess) return -1;
+  return v;
+}
+
+template <int N>
+static cudaError_t cols_tma_n(float* spec, const float* Kp, const float* Kb, int L, const float* twf, cudaStream_t s) {
+  using G = ColTma<N>;
+  ColMaps maps;
+  if (!fft_map(&maps.spec, spec, (size_t)L * N, N, 2 * G::C, G::BR) ||
+      !fft_map(&maps.k, Kp, (size_t)L * N, N / 2, G::C, G::BR))
+    return cudaErrorNotSupported;
+  static int resident = 0;
+  if (!resident) {
+    int dev = 0, sms = 1, occ = 1;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_cols_tma<N>, G::C * (N / 8), G::SMEM) != cudaSuccess ||
+        occ < 1)
+      occ = 1;
+    resident = (sms > 0 ? sms : 1) * occ;
+  }
+  const int ntiles = L * (N / 2 / G::C);
+  k_cols_tma<N><<<ntiles < resident ? ntiles : resident, G::C * (N / 8), G::SMEM, s>>>(
+      maps, Kb, reinterpret_cast<const cpx<float>*>(twf), ntiles);
+  return cudaGetLastError();
 }
 
 // ------------------------------------------------------------------ FP32 rows inverse + primal
@@ -351,6 +543,14 @@ template <int N> static cudaError_t cols_filter_n(float* spec, const float* Kp, 
 
 cudaError_t launch_cols_filter(float* spec, const float* Kp, const float* Kb, int n, int L, const float* twf,
                                cudaStream_t s) {
+  // the pipelined kernel for the larger planes (16-byte aligned arrays; MUFFIN_COLS_PLAIN: the plain one)
+  if ((n == 256 || n == 512) && ((uintptr_t)spec & 15) == 0 && ((uintptr_t)Kp & 15) == 0 &&
+      getenv("MUFFIN_COLS_PLAIN") == nullptr) {
+    switch (n) {
+      case 256: return cols_tma_n<256>(spec, Kp, Kb, L, twf, s);
+      case 512: return cols_tma_n<512>(spec, Kp, Kb, L, twf, s);
+    }
+  }
 #define CALL(NN) return cols_filter_n<NN>(spec, Kp, Kb, L, twf, s);
   MUFFIN_N_SWITCH(n, CALL)
 #undef CALL
@@ -467,6 +667,9 @@ cudaError_t launch_max_abs2(const void* hhat, const double* w, int n, int L, dou
 // context before any launch (and so before any stream capture).
 template <int N> static cudaError_t configure_n() {
   cudaError_t e;
+  if constexpr (N == 256 || N == 512) {
+    if ((e = allow_max_dyn_smem(k_cols_tma<N>))) return e;
+  }
   if ((e = allow_max_dyn_smem(k_cols_filter<N>))) return e;
   if ((e = allow_max_dyn_smem(k_c2c_rows64<N, -1>))) return e;
   if ((e = allow_max_dyn_smem(k_c2c_rows64<N, 1>))) return e;

@@ -889,6 +889,7 @@ cudaError_t launch_fine_analysis(const Geom& g, const IuwtArgs& a, int mode, cud
     return cudaGetLastError();
   }
   if (nblocks) *nblocks = (g.n / kTile) * (g.n / kTile) * g.L;
+  if (g.vec && mode == MODE_UPDATE && iuwt_vec_fine_ok(g)) return launch_fine_analysis_vec(g, a, s);
   switch (g.gen * 10 + g.j1) {
     case 11: return fine_an_mode<1, 1>(g, a, mode, s);
     case 12: return fine_an_mode<1, 2>(g, a, mode, s);
@@ -917,6 +918,7 @@ template <int GEN, int J1> static cudaError_t fine_adj(const Geom& g, const Iuwt
 }
 
 cudaError_t launch_fine_adjoint(const Geom& g, const IuwtArgs& a, cudaStream_t s) {
+  if (g.vec && iuwt_vec_fine_ok(g)) return launch_fine_adjoint_vec(g, a, s);
   switch (g.gen * 10 + g.j1) {
     case 11: return fine_adj<1, 1>(g, a, s);
     case 12: return fine_adj<1, 2>(g, a, s);
@@ -969,6 +971,10 @@ static cudaError_t coarse_n(const Geom& g, const float* c_in, float* r_out, floa
 
 cudaError_t launch_coarse(const Geom& g, const float* c_in, float* r_out, float* U, float k, float rho, int mode,
                           double* partials, cudaStream_t s, int* nblocks) {
+  if (g.vec && mode == MODE_UPDATE && iuwt_vec_coarse_ok(g)) {
+    if (nblocks) *nblocks = (1 << (2 * g.j1)) * g.L;
+    return launch_coarse_vec(g, c_in, r_out, U, k, rho, s);
+  }
   if (nblocks) *nblocks = (1 << (2 * g.j1)) * g.L * (g.cs > 0 ? g.cs : 1);
 #define CO(GEN)                                                                                            \
   switch (mode) {                                                                                          \
@@ -1050,6 +1056,14 @@ template <int GEN> static cudaError_t cfg_gen(Geom& g) {
   return cudaSuccess;
 }
 
-cudaError_t iuwt_configure(Geom& g) { return g.gen == 1 ? cfg_gen<1>(g) : cfg_gen<2>(g); }
+cudaError_t iuwt_configure(Geom& g) {
+  // MUFFIN_IUWT_GENERAL: the general kernels for every generation (comparisons)
+  g.vec = (g.gen == 1 && getenv("MUFFIN_IUWT_GENERAL") == nullptr) ? 1 : 0;
+  if (g.vec) {
+    const cudaError_t e = iuwt_vec_configure();
+    if (e != cudaSuccess) return e;
+  }
+  return g.gen == 1 ? cfg_gen<1>(g) : cfg_gen<2>(g);
+}
 
 }  // namespace muffin

@@ -18,6 +18,7 @@ namespace {
 
 thread_local std::string g_init_error;
 constexpr int kNumStages = 7;
+constexpr int kSideStreams = 4;    // graph branches of one pass: up to 3 group branches and the spectral step
 const char* kStageNames[kNumStages] = {"iuwt_fine_adjoint", "fft_rows_fwd", "fft_cols_filter", "fft_rows_inv_primal",
                                        "iuwt_fine_analysis", "iuwt_coarse", "spectral_dct"};
 
@@ -85,6 +86,10 @@ int check(const muffin_params* p, std::string* why) {
   }
   return MUFFIN_OK;
 }
+
+// Default pass plan: the whole cube as one group, one branch.
+int default_group(const muffin_params*) { return 0; }
+int default_branches(const muffin_params*) { return 1; }
 
 struct Layout {
   size_t X, U, V, y, b, Kp, Kb, spec, S, T, D, cr, hhat, yhat, z64, pw, partials, scal;
@@ -164,6 +169,12 @@ struct muffin_ctx {
   cudaGraphExec_t exec = nullptr;
   unsigned version = 0;    // bumped whenever the pass changes (step sizes, weights, tiling)
   std::string err;
+  // pass plan: channels per group (the FFT and wavelet kernels of one group run
+  // back to back, so that its row spectra and c_j1 / r_j1 stay in L2) and the
+  // number of graph branches the groups alternate between
+  int group = 0, branches = 1;
+  cudaStream_t side[kSideStreams] = {};
+  std::vector<cudaEvent_t> ev;     // fork, per-group "D written", per-branch join
 
   template <typename T> T* at(size_t off) const { return reinterpret_cast<T*>(ws + off); }
   float* X() const { return at<float>(lo.X); }
@@ -229,78 +240,142 @@ struct StageTimer {
   }
 };
 
+// Channel groups and branches of one pass (see the context's plan).
+static void pass_plan(const muffin_ctx* ctx, bool timed, int* G, int* ngroups, int* nb) {
+  const Geom& g = ctx->g;
+  // the union-of-bases kernels take the whole cube in one launch
+  *G = (timed || g.dict || ctx->group <= 0 || ctx->group >= g.L) ? g.L : ctx->group;
+  *ngroups = (g.L + *G - 1) / *G;
+  int b = ctx->branches < 1 ? 1 : ctx->branches;
+  if (b > kSideStreams - 1) b = kSideStreams - 1;
+  if (b > *ngroups) b = *ngroups;
+  *nb = timed ? 1 : b;
+}
+
+// One pass of Algorithm 1.  Per channel group: the gradient FFTs ending in the
+// primal step (Eqs. 8, 10), the spatial analysis with the dual update (Eq. 11)
+// and the spatial adjoint W_s^T U of the updated duals, which the next pass's
+// primal step reads (Eq. 9).  The spectral step (Eqs. 13-14 and the next
+// pass's T) needs every channel of a pixel: it waits for every group's D and
+// runs on its own branch, beside the remaining wavelet kernels.  Timed passes
+// (tm) run everything in order on s, one group.
 static int enqueue_pass(muffin_ctx* ctx, cudaStream_t s, StageTimer* tm) {
   const Geom& g = ctx->g;
   const Layout& lo = ctx->lo;
   const bool spatial = ctx->mu_s != 0.0, spectral = ctx->mu_l != 0.0;
-  IuwtArgs ia{};
-  ia.D = ctx->at<float>(lo.D);
-  ia.U = ctx->U();
-  ia.cr = ctx->at<float>(lo.cr);
-  ia.rin = ctx->at<float>(lo.cr);
-  ia.S = ctx->at<float>(lo.S);
-  ia.k = (float)(ctx->sigma * ctx->mu_s);
-  ia.rho = (float)ctx->rho;
+  const size_t P = ctx->P();
+  int G, ngroups, nb;
+  pass_plan(ctx, tm != nullptr, &G, &ngroups, &nb);
+  const bool fork = !tm && (nb > 1 || spectral);
   auto mark = [&](int k) { if (tm) tm->mark(k); };
   mark(-1);
-  if (spatial && g.dict) {
-    CK(launch_dwt_adjoint(g, ctx->dwt(nullptr), s));
-    mark(0);
-  } else if (spatial && g.J > 0 && g.j1 > 0) {
-    CK(launch_fine_adjoint(g, ia, s));
-    mark(0);
+  // events: [0] fork, [1 .. ngroups] D of group written, then one join per branch
+  const size_t nev = 1 + (size_t)ngroups + kSideStreams;
+  while (ctx->ev.size() < nev) {
+    cudaEvent_t e;
+    CK(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+    ctx->ev.push_back(e);
   }
-  CK(launch_rows_fwd(ctx->X(), ctx->at<float>(lo.spec), g.n, g.L, ctx->at<float>(lo.twf), s));
-  mark(1);
-  CK(launch_cols_filter(ctx->at<float>(lo.spec), ctx->at<float>(lo.Kp), ctx->at<float>(lo.Kb), g.n, g.L,
-                        ctx->at<float>(lo.twf), s));
-  mark(2);
-  PrimalArgs pa{};
-  pa.b = ctx->at<float>(lo.b);
-  pa.S = spatial ? ctx->S_ptr() : nullptr;
-  pa.T = spectral ? ctx->at<float>(lo.T) : nullptr;
-  pa.X = ctx->X();
-  pa.D = ctx->at<float>(lo.D);
-  pa.tau = (float)ctx->tau;
-  pa.mu_s = (float)ctx->mu_s;
-  pa.mu_l = (float)ctx->mu_l;
-  pa.rho = (float)ctx->rho;
-  CK(launch_rows_inv_primal(ctx->at<float>(lo.spec), pa, g.n, g.L, ctx->at<float>(lo.twf), s));
-  mark(3);
-  if (spatial && g.dict) {
-    CK(launch_dwt_analysis(g, ctx->dwt(ctx->at<float>(lo.D)), MODE_UPDATE, s));
-    mark(4);
-  } else if (spatial) {
+  cudaStream_t br[kSideStreams];
+  br[0] = s;
+  for (int b = 1; b < nb; ++b) br[b] = ctx->side[b - 1];
+  if (fork) {
+    CK(cudaEventRecord(ctx->ev[0], s));
+    for (int b = 1; b < nb; ++b) CK(cudaStreamWaitEvent(br[b], ctx->ev[0], 0));
+  }
+  const float k_s = (float)(ctx->sigma * ctx->mu_s), rho = (float)ctx->rho;
+  for (int gi = 0; gi < ngroups; ++gi) {
+    const int b = gi % nb;
+    cudaStream_t st = br[b];
+    const int l0 = gi * G, Lg = G < g.L - l0 ? G : g.L - l0;
+    Geom gg = g;
+    gg.L = Lg;
+    const size_t o = (size_t)l0 * P;
+    float* spec = ctx->at<float>(lo.spec) + (size_t)b * G * P;
+    float* cr = ctx->at<float>(lo.cr) + (size_t)b * G * P;
+    CK(launch_rows_fwd(ctx->X() + o, spec, g.n, Lg, ctx->at<float>(lo.twf), st));
+    mark(1);
+    CK(launch_cols_filter(spec, ctx->at<float>(lo.Kp) + (size_t)l0 * g.n * (g.n / 2),
+                          ctx->at<float>(lo.Kb) + (size_t)l0 * g.n, g.n, Lg, ctx->at<float>(lo.twf), st));
+    mark(2);
+    PrimalArgs pa{};
+    pa.b = ctx->at<float>(lo.b) + o;
+    pa.S = spatial ? ((g.J == 0 && g.dict == 0) ? ctx->U() + o : ctx->at<float>(lo.S) + o) : nullptr;
+    pa.T = spectral ? ctx->at<float>(lo.T) + o : nullptr;
+    pa.X = ctx->X() + o;
+    pa.D = ctx->at<float>(lo.D) + o;
+    pa.tau = (float)ctx->tau;
+    pa.mu_s = (float)ctx->mu_s;
+    pa.mu_l = (float)ctx->mu_l;
+    pa.rho = rho;
+    CK(launch_rows_inv_primal(spec, pa, g.n, Lg, ctx->at<float>(lo.twf), st));
+    mark(3);
+    if (fork && spectral) CK(cudaEventRecord(ctx->ev[1 + gi], st));
+    if (!spatial) continue;
+    if (g.dict) {
+      DwtArgs da = ctx->dwt(ctx->at<float>(lo.D));
+      CK(launch_dwt_analysis(g, da, MODE_UPDATE, st));
+      mark(4);
+      CK(launch_dwt_adjoint(g, ctx->dwt(nullptr), st));
+      mark(0);
+      continue;
+    }
+    IuwtArgs ia{};
+    ia.D = ctx->at<float>(lo.D) + o;
+    ia.U = ctx->U() + o * ctx->planes();
+    ia.cr = cr;
+    ia.rin = cr;
+    ia.S = ctx->at<float>(lo.S) + o;
+    ia.k = k_s;
+    ia.rho = rho;
     if (g.j1 > 0 || g.J == 0) {
-      CK(launch_fine_analysis(g, ia, MODE_UPDATE, s, nullptr));
+      CK(launch_fine_analysis(gg, ia, MODE_UPDATE, st, nullptr));
       mark(4);
     }
     if (g.J > g.j1) {
-      const float* cin = g.j1 > 0 ? ctx->at<float>(lo.cr) : ctx->at<float>(lo.D);
-      float* rout = g.j1 > 0 ? ctx->at<float>(lo.cr) : ctx->at<float>(lo.S);
-      CK(launch_coarse(g, cin, rout, ctx->U(), ia.k, ia.rho, MODE_UPDATE, nullptr, s, nullptr));
+      CK(launch_coarse(gg, g.j1 > 0 ? cr : ia.D, g.j1 > 0 ? cr : ia.S, ia.U, k_s, rho, MODE_UPDATE, nullptr, st,
+                       nullptr));
       mark(5);
+    }
+    if (g.J > 0 && g.j1 > 0) {
+      CK(launch_fine_adjoint(gg, ia, st));
+      mark(0);
     }
   }
   if (spectral) {
+    cudaStream_t sp = s;
+    if (fork) {
+      sp = ctx->side[kSideStreams - 1];
+      for (int gi = 0; gi < ngroups; ++gi) CK(cudaStreamWaitEvent(sp, ctx->ev[1 + gi], 0));
+    }
     SpecArgs sa{};
     sa.D = ctx->at<float>(lo.D);
     sa.V = ctx->V();
     sa.T = ctx->at<float>(lo.T);
     sa.k = (float)(ctx->sigma * ctx->mu_l);
-    sa.rho = (float)ctx->rho;
+    sa.rho = rho;
     sa.tw = ctx->at<float>(lo.twL);
     sa.post = ctx->at<float>(lo.post);
     sa.pre = ctx->at<float>(lo.pre);
     sa.invs = ctx->at<float>(lo.invs);
     sa.dense = ctx->at<float>(lo.dense);
-    CK(launch_spectral(sa, (int)ctx->P(), g.L, SPEC_UPDATE, s, nullptr));
+    CK(launch_spectral(sa, (int)P, g.L, SPEC_UPDATE, sp, nullptr));
     mark(6);
+    if (fork) {
+      CK(cudaEventRecord(ctx->ev[1 + ngroups], sp));
+      CK(cudaStreamWaitEvent(s, ctx->ev[1 + ngroups], 0));
+    }
+  }
+  if (fork) {
+    for (int b = 1; b < nb; ++b) {
+      CK(cudaEventRecord(ctx->ev[2 + ngroups + b], br[b]));
+      CK(cudaStreamWaitEvent(s, ctx->ev[2 + ngroups + b], 0));
+    }
   }
   return MUFFIN_OK;
 }
 
-// T = W_lambda^T V and r_{j1} of W_s^T U from the stored duals (after a state load).
+// T = W_lambda^T V and S = W_s^T U from the stored duals (after a state load).
 static int refresh_adjoints(muffin_ctx* ctx) {
   const Geom& g = ctx->g;
   const Layout& lo = ctx->lo;
@@ -317,9 +392,18 @@ static int refresh_adjoints(muffin_ctx* ctx) {
   CK(launch_spectral(sa, (int)ctx->P(), g.L, SPEC_TONLY, ctx->stream, nullptr));
   if (g.dict) {
     CK(launch_dwt_adjoint(g, ctx->dwt(nullptr), ctx->stream));
-  } else if (g.J > g.j1) {
+    return MUFFIN_OK;
+  }
+  if (g.J > g.j1) {
     float* rout = g.j1 > 0 ? ctx->at<float>(lo.cr) : ctx->at<float>(lo.S);
     CK(launch_coarse(g, nullptr, rout, ctx->U(), 0.f, 1.f, MODE_ADJ, nullptr, ctx->stream, nullptr));
+  }
+  if (g.J > 0 && g.j1 > 0) {
+    IuwtArgs ia{};
+    ia.U = ctx->U();
+    ia.rin = ctx->at<float>(lo.cr);
+    ia.S = ctx->at<float>(lo.S);
+    CK(launch_fine_adjoint(g, ia, ctx->stream));
   }
   return MUFFIN_OK;
 }
@@ -466,9 +550,25 @@ int muffin_init(muffin_ctx** out, const muffin_params* p, const float* d_dirty, 
                     getenv("MUFFIN_NO_AUTOTUNE") == nullptr;
   ctx->tau = p->tau > 0 ? p->tau : 0.0;
   if (ctx->p.power_iters <= 0) ctx->p.power_iters = 40;
-  auto bail = [&](int code) { if (ctx->cap) cudaStreamDestroy(ctx->cap); g_init_error = ctx->err; delete ctx; return code; };
+  auto bail = [&](int code) {
+    if (ctx->cap) cudaStreamDestroy(ctx->cap);
+    for (cudaStream_t x : ctx->side) if (x) cudaStreamDestroy(x);
+    g_init_error = ctx->err;
+    delete ctx;
+    return code;
+  };
   cudaError_t e;
   if ((e = cudaStreamCreateWithFlags(&ctx->cap, cudaStreamNonBlocking))) { fail(ctx, MUFFIN_ERR_CUDA, "cudaStreamCreate", cudaGetErrorString(e)); return bail(MUFFIN_ERR_CUDA); }
+  for (int b = 0; b < kSideStreams; ++b)
+    if ((e = cudaStreamCreateWithFlags(&ctx->side[b], cudaStreamNonBlocking))) {
+      fail(ctx, MUFFIN_ERR_CUDA, "cudaStreamCreate", cudaGetErrorString(e));
+      return bail(MUFFIN_ERR_CUDA);
+    }
+  // pass plan (channels per group, graph branches); MUFFIN_GROUP / MUFFIN_BRANCHES override
+  ctx->group = default_group(p);
+  ctx->branches = default_branches(p);
+  if (const char* v = getenv("MUFFIN_GROUP")) ctx->group = atoi(v);
+  if (const char* v = getenv("MUFFIN_BRANCHES")) ctx->branches = atoi(v);
   if ((e = fft_configure(ctx->g.n)) || (ctx->g.dict == 0 && (e = iuwt_configure(ctx->g))) ||
       (ctx->g.dict == 1 && (e = dwt_configure())) || (e = spectral_configure(ctx->g.L))) {
     fail(ctx, MUFFIN_ERR_CUDA, "kernel configuration", cudaGetErrorString(e));
@@ -719,6 +819,11 @@ int muffin_objective(muffin_ctx* ctx, double* h_obj, double* h_terms) {
   double h[4];
   CK(cudaMemcpyAsync(h, sc + 10, sizeof(h), cudaMemcpyDeviceToHost, s));
   CK(cudaStreamSynchronize(s));
+  // a block of the pipelined spectral kernel that gave up a bounded wait left its tiles unwritten
+  const int to = spectral_take_timeouts(), tf = fft_take_timeouts();
+  if (to < 0 || tf < 0) return fail(ctx, MUFFIN_ERR_CUDA, "reading the pipelined kernels' wait status");
+  if (to > 0 || tf > 0)
+    return fail(ctx, MUFFIN_ERR_TIMEOUT, "a block of a pipelined (TMA) kernel gave up a bounded wait; the state is incomplete");
   const double data = h[0], sp = ctx->mu_s * (h[1] + h[2]), sl = ctx->mu_l * h[3];
   *h_obj = data + sp + sl;
   if (h_terms) { h_terms[0] = data; h_terms[1] = sp; h_terms[2] = sl; }
@@ -822,10 +927,32 @@ double muffin_stage_bytes(const muffin_ctx* ctx, int k) {
 
 int muffin_kernels_per_iteration(const muffin_ctx* ctx) {
   if (!ctx) return 0;
-  int n = 0;
-  for (int k = 0; k < kNumStages; ++k) n += muffin_stage_bytes(ctx, k) > 0 ? 1 : 0;
+  int G, ngroups, nb;
+  pass_plan(ctx, false, &G, &ngroups, &nb);
+  int per_group = 0;
+  for (int k = 0; k < kNumStages; ++k) per_group += (k != 6 && muffin_stage_bytes(ctx, k) > 0) ? 1 : 0;
+  int n = ngroups * per_group + (muffin_stage_bytes(ctx, 6) > 0 ? 1 : 0);
   if (ctx->g.dict && ctx->mu_s != 0.0) n += 3 * ctx->g.J - 2;   // 2J adjoint and J analysis kernels, not 2
   return n;
+}
+
+int muffin_set_plan(muffin_ctx* ctx, int channels_per_group, int branches) {
+  if (!ctx) return fail(nullptr, MUFFIN_ERR_ARG, "ctx is NULL");
+  if (channels_per_group < 0 || branches < 1 || branches > kSideStreams - 1)
+    return fail(ctx, MUFFIN_ERR_ARG, "channels_per_group must be >= 0 and branches in [1, 3]");
+  ctx->group = channels_per_group;
+  ctx->branches = branches;
+  drop_graph(ctx);
+  return MUFFIN_OK;
+}
+
+int muffin_plan(const muffin_ctx* ctx, int* channels_per_group, int* branches) {
+  if (!ctx) return MUFFIN_ERR_ARG;
+  int G, ngroups, nb;
+  pass_plan(ctx, false, &G, &ngroups, &nb);
+  if (channels_per_group) *channels_per_group = G;
+  if (branches) *branches = nb;
+  return MUFFIN_OK;
 }
 
 int muffin_tiling(const muffin_ctx* ctx, int* fine_levels, int* cluster) {
@@ -841,6 +968,8 @@ void muffin_destroy(muffin_ctx* ctx) {
   if (!ctx) return;
   drop_graph(ctx);
   if (ctx->cap) cudaStreamDestroy(ctx->cap);
+  for (cudaStream_t x : ctx->side) if (x) cudaStreamDestroy(x);
+  for (cudaEvent_t e : ctx->ev) cudaEventDestroy(e);
   delete ctx;
 }
 

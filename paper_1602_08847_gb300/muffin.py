@@ -56,6 +56,8 @@ def _load():
         "muffin_set_mu": (I, [P, D, D]),
         "muffin_step_sizes": (I, [P, pd, pd, pd, pd, pd, pd, pd]),
         "muffin_iterate_timed": (I, [P, I, pd, I]),
+        "muffin_set_plan": (I, [P, I, I]),
+        "muffin_plan": (I, [P, ctypes.POINTER(I), ctypes.POINTER(I)]),
         "muffin_num_stages": (I, []),
         "muffin_stage_name": (ctypes.c_char_p, [I]),
         "muffin_stage_bytes": (D, [P, I]),
@@ -220,6 +222,15 @@ class Muffin:
 
     def kernels_per_iteration(self) -> int:
         return int(_lib.muffin_kernels_per_iteration(self._ctx))
+
+    def set_plan(self, channels_per_group: int, branches: int = 1):
+        """Channels per group of the pass (0: whole cube) and graph branches (1..3)."""
+        self._check(_lib.muffin_set_plan(self._ctx, int(channels_per_group), int(branches)))
+
+    def plan(self) -> tuple[int, int]:
+        g, b = ctypes.c_int(), ctypes.c_int()
+        self._check(_lib.muffin_plan(self._ctx, ctypes.byref(g), ctypes.byref(b)))
+        return g.value, b.value
 
     def tiling(self) -> tuple[int, int]:
         j1, cs = ctypes.c_int(), ctypes.c_int()
