@@ -15,6 +15,8 @@
 // bank groups.  The taps are summed unnormalised, (a + e) + 4 (b + d) + 6 c,
 // and the 1/256 of the two passes is applied once in the epilogue.
 // Global loads and stores of the natural-layout planes are 128-bit.
+#include <cstdlib>
+
 #include "device.cuh"
 #include "internal.h"
 
@@ -22,7 +24,32 @@ namespace muffin {
 namespace vec {
 
 constexpr int kT = 64;          // output tile side (fine kernels)
-constexpr int kNT = 256;        // threads per block
+// Threads per block: NT is a template parameter of every kernel (256 or 512).
+
+// Outputs per work item of a vertical pass (chains of RO / D rows over NCH
+// chunk columns) and of a horizontal pass (rows of NCO chunks), chosen for NT
+// threads: the least per-thread work, counted as rounds of items times
+// (outputs + window loads), ties to the longer run (fewer window reloads).
+__host__ __device__ constexpr int choose_seg(int NT, int NCH, int RO, int D) {
+  int best = 1, best_cost = 1 << 30;
+  const int chain = (RO + D - 1) / D;
+  for (int seg = 2; seg <= 11 && seg <= chain; ++seg) {
+    const int items = NCH * D * ((chain + seg - 1) / seg);
+    const int cost = ((items + NT - 1) / NT) * (2 * seg + 4);
+    if (cost <= best_cost) { best_cost = cost; best = seg; }
+  }
+  return best;
+}
+__host__ __device__ constexpr int choose_segc(int NT, int NR, int NCO, int D) {
+  int best = 1, best_cost = 1 << 30;
+  const int kr = (2 * D + 3) / 4;
+  for (int seg = 2; seg <= 11 && seg <= NCO; ++seg) {
+    const int items = NR * ((NCO + seg - 1) / seg);
+    const int cost = ((items + NT - 1) / NT) * (2 * seg + 2 * kr);
+    if (cost <= best_cost) { best_cost = cost; best = seg; }
+  }
+  return best;
+}
 
 __host__ __device__ constexpr int ceil4(int v) { return (v + 3) & ~3; }
 
@@ -49,14 +76,14 @@ __device__ __forceinline__ float4 b3u4(const float4& a, const float4& b, const f
 // the output origin).  DIFF: the input is in - sub (both read at the same place).
 // A work item is a chain segment: chunk column c (fastest across threads),
 // residue rho = o mod D, SEG outputs.
-template <int D, int NCH, int RO, int SEG, int PI, int PO, bool DIFF>
+template <int NT, int D, int NCH, int RO, int SEG, int PI, int PO, bool DIFF>
 __device__ __forceinline__ void vpass(const float* __restrict__ in, const float* __restrict__ sub,
                                       float* __restrict__ out) {
   constexpr int CHAIN = (RO + D - 1) / D;
   constexpr int NSEG = (CHAIN + SEG - 1) / SEG;
   constexpr int NITEMS = NCH * D * NSEG;
   constexpr int RIN = RO + 4 * D;
-  for (int it = threadIdx.x; it < NITEMS; it += kNT) {
+  for (int it = threadIdx.x; it < NITEMS; it += NT) {
     const int c = it % NCH;
     const int rest = it / NCH;
     const int rho = rest % D;
@@ -85,13 +112,13 @@ __device__ __forceinline__ void vpass(const float* __restrict__ in, const float*
 // KO is the input chunk of output chunk 0 (input chunk index 0 = in).
 // epi(r, k, raw) receives the float4 of raw sums.  A work item is a run of SEGC
 // output chunks of one row (rows fastest across threads).
-template <int D, int NR, int NCO, int SEGC, int KO, int PI, typename F>
+template <int NT, int D, int NR, int NCO, int SEGC, int KO, int PI, typename F>
 __device__ __forceinline__ void hpass(const float* __restrict__ in, F&& epi) {
   constexpr int KR = (2 * D + 3) / 4;          // input chunks needed on each side
   constexpr int NSEG = (NCO + SEGC - 1) / SEGC;
   constexpr int NITEMS = NR * NSEG;
   constexpr int NW = SEGC + 2 * KR;
-  for (int it = threadIdx.x; it < NITEMS; it += kNT) {
+  for (int it = threadIdx.x; it < NITEMS; it += NT) {
     const int r = it % NR;
     const int s = it / NR;
     const int k0 = s * SEGC;
@@ -123,14 +150,14 @@ __device__ __forceinline__ void hpass(const float* __restrict__ in, F&& epi) {
 
 // Same along a periodic row of NCH chunks (coarse sub-images): input chunk
 // (k + q) mod NCH.
-template <int D, int NR, int NCH, int SEGC, int PI, typename F>
+template <int NT, int D, int NR, int NCH, int SEGC, int PI, typename F>
 __device__ __forceinline__ void hpass_per(const float* __restrict__ in, F&& epi) {
   constexpr int KR = (2 * D + 3) / 4;
   constexpr int NSEG = NCH / SEGC;
   static_assert(NCH % SEGC == 0, "periodic rows split into whole runs");
   constexpr int NITEMS = NR * NSEG;
   constexpr int NW = SEGC + 2 * KR;
-  for (int it = threadIdx.x; it < NITEMS; it += kNT) {
+  for (int it = threadIdx.x; it < NITEMS; it += NT) {
     const int r = it % NR;
     const int s = it / NR;
     const int k0 = s * SEGC;
@@ -169,16 +196,16 @@ __device__ __forceinline__ float4 dual4(float4 uo, float4 w, float k, float rho)
 // ty0 - HY .. ty0 + 64 + HY - 1, columns tx0 - HX .. tx0 + 64 + HX - 1 (HX a
 // multiple of 4), as float4 chunks, into dst (pitch P).  Loads then stores,
 // NPT chunks per thread in flight.
-template <int HY, int HX, int P>
+template <int NT, int HY, int HX, int P>
 struct Region {
   static constexpr int ROWS = kT + 2 * HY, NCH = (kT + 2 * HX) / 4, N4 = ROWS * NCH;
-  static constexpr int NPT = (N4 + kNT - 1) / kNT;
+  static constexpr int NPT = (N4 + NT - 1) / NT;
   float4 v[NPT];
   __device__ __forceinline__ void load(const float* __restrict__ plane, int n, int ty0, int tx0) {
     const int m = n - 1;
 #pragma unroll
     for (int q = 0; q < NPT; ++q) {
-      const int i = threadIdx.x + q * kNT;
+      const int i = threadIdx.x + q * NT;
       if (i < N4) {
         const int r = i / NCH, c = i % NCH;
         const int gy = (ty0 - HY + r) & m, gx = (tx0 - HX + 4 * c) & m;
@@ -191,7 +218,7 @@ struct Region {
   __device__ __forceinline__ void store(float* __restrict__ dst) const {
 #pragma unroll
     for (int q = 0; q < NPT; ++q) {
-      const int i = threadIdx.x + q * kNT;
+      const int i = threadIdx.x + q * NT;
       if (i < N4) {
         const int r = i / NCH, c = i % NCH;
         st4(dst + (r + R0) * P + 4 * (c + C0), v[q]);
@@ -216,7 +243,7 @@ template <int J1> struct FineA {
   static constexpr size_t SMEM = (size_t)(2 * NA + NW) * sizeof(float);
 };
 
-template <int J1, int J0>
+template <int NT, int J1, int J0>
 __device__ __forceinline__ void fine_an_level(float* __restrict__ A, float* __restrict__ T, float* __restrict__ W,
                                               float* __restrict__ Uj, int n, int ty0, int tx0, float k, float rho) {
   using G = FineA<J1>;
@@ -226,19 +253,20 @@ __device__ __forceinline__ void fine_an_level(float* __restrict__ A, float* __re
   constexpr int R0 = G::HC(0) - HCo;                // region row of output row 0
   constexpr int C0 = (G::HX(0) - HXo) / 4;          // region chunk of output chunk 0
   // this thread's four chunks of U_j on the tile; they arrive during the passes
-  float4 uo[4];
+  constexpr int NU = kT * kT / 4 / NT;
+  float4 uo[NU];
 #pragma unroll
-  for (int q = 0; q < 4; ++q) {
-    const int i = threadIdx.x + q * kNT, r = i >> 4, c = i & 15;
+  for (int q = 0; q < NU; ++q) {
+    const int i = threadIdx.x + q * NT, r = i >> 4, c = i & 15;
     uo[q] = ldg4(Uj + (size_t)(ty0 + r) * n + tx0 + 4 * c);
   }
-  constexpr int SEGV = J0 == 0 ? 11 : (J0 == 1 ? 10 : 8);
-  vpass<D, NCHI, RO, SEGV, PA, PA, false>(A + (G::HC(0) - HCi) * PA + (G::HX(0) - HXi),
+  constexpr int SEGV = choose_seg(NT, NCHI, RO, D);
+  vpass<NT, D, NCHI, RO, SEGV, PA, PA, false>(A + (G::HC(0) - HCi) * PA + (G::HX(0) - HXi),
                                           nullptr, T + R0 * PA + (G::HX(0) - HXi));
   __syncthreads();
-  constexpr int SEGC = NCO % 11 == 0 ? 11 : (NCO % 10 == 0 ? 10 : (NCO % 9 == 0 ? 9 : 8));
+  constexpr int SEGC = choose_segc(NT, RO, NCO, D);
   constexpr float inv = 1.0f / 256.0f;
-  hpass<D, RO, NCO, SEGC, (HXi - HXo) / 4, PA>(
+  hpass<NT, D, RO, NCO, SEGC, (HXi - HXo) / 4, PA>(
       T + R0 * PA + (G::HX(0) - HXi), [&](int r, int kc, float4 raw) {
         float* a = A + (R0 + r) * PA + 4 * (C0 + kc);
         const float4 cj = ld4(a);
@@ -249,18 +277,18 @@ __device__ __forceinline__ void fine_an_level(float* __restrict__ A, float* __re
       });
   __syncthreads();
 #pragma unroll
-  for (int q = 0; q < 4; ++q) {
-    const int i = threadIdx.x + q * kNT, r = i >> 4, c = i & 15;
+  for (int q = 0; q < NU; ++q) {
+    const int i = threadIdx.x + q * NT, r = i >> 4, c = i & 15;
     const float4 w = ld4(W + r * PW + 4 * c);
     float4* dst = reinterpret_cast<float4*>(Uj + (size_t)(ty0 + r) * n + tx0 + 4 * c);
     *dst = dual4(uo[q], w, k, rho);
   }
-  if constexpr (J0 + 1 < J1) fine_an_level<J1, J0 + 1>(A, T, W, Uj + (size_t)n * n, n, ty0, tx0, k, rho);
+  if constexpr (J0 + 1 < J1) fine_an_level<NT, J1, J0 + 1>(A, T, W, Uj + (size_t)n * n, n, ty0, tx0, k, rho);
 }
 
 // One 64 x 64 tile (origin ty0, tx0) of channel l; sm: FineA<J1>::SMEM bytes.
 // U: [L][J+1][n][n]; planes j >= J1 class-permuted.
-template <int J1>
+template <int NT, int J1>
 __device__ __forceinline__ void fine_analysis_tile(float* __restrict__ sm, int n, int J, const float* __restrict__ D,
                                                    float* __restrict__ U, float* __restrict__ cr, float k, float rho,
                                                    int l, int ty0, int tx0) {
@@ -270,18 +298,18 @@ __device__ __forceinline__ void fine_analysis_tile(float* __restrict__ sm, int n
   float* W = T + G::NA;
   const size_t P = (size_t)n * n;
   {
-    Region<G::HC(0), G::HX(0), G::PA> reg;
+    Region<NT, G::HC(0), G::HX(0), G::PA> reg;
     reg.load(D + (size_t)l * P, n, ty0, tx0);
     reg.template store<0, 0>(A);
   }
   __syncthreads();
-  fine_an_level<J1, 0>(A, T, W, U + (size_t)l * (J + 1) * P, n, ty0, tx0, k, rho);
+  fine_an_level<NT, J1, 0>(A, T, W, U + (size_t)l * (J + 1) * P, n, ty0, tx0, k, rho);
   // c_J1 on the tile -> class-permuted (stride S = 2^J1): one float4 = 4 sub-columns of one class
   constexpr int S = 1 << J1, NSUB = kT / S / 4;   // float4 per class per tile row
   const int mc = n >> J1;
   const size_t mc2 = (size_t)mc * mc;
   float* dst = J == J1 ? U + ((size_t)l * (J + 1) + J) * P : cr + (size_t)l * P;
-  for (int i = threadIdx.x; i < kT * S * NSUB; i += kNT) {
+  for (int i = threadIdx.x; i < kT * S * NSUB; i += NT) {
     const int cx = i % S, rest = i / S, m4 = rest % NSUB, r = rest / NSUB;
     const float* a = A + (G::HC(0) + r) * G::PA + G::HX(0) + cx + S * 4 * m4;
     float4 v = make_float4(a[0], a[S], a[2 * S], a[3 * S]);
@@ -293,12 +321,12 @@ __device__ __forceinline__ void fine_analysis_tile(float* __restrict__ sm, int n
 }
 
 // grid (n/64, n/64, L)
-template <int J1>
-__global__ void __launch_bounds__(kNT, 2)
+template <int NT, int J1>
+__global__ void __launch_bounds__(NT, 2)
 k_fine_analysis_v(int n, int J, const float* __restrict__ D, float* __restrict__ U, float* __restrict__ cr,
                   float k, float rho) {
   extern __shared__ __align__(16) float sm[];
-  fine_analysis_tile<J1>(sm, n, J, D, U, cr, k, rho, blockIdx.z, blockIdx.y * kT, blockIdx.x * kT);
+  fine_analysis_tile<NT, J1>(sm, n, J, D, U, cr, k, rho, blockIdx.z, blockIdx.y * kT, blockIdx.x * kT);
 }
 
 // ================================================================== fine adjoint (generation 1)
@@ -315,7 +343,7 @@ template <int J1> struct FineT {
   static constexpr size_t SMEM = (size_t)(2 * NA + NT) * sizeof(float);
 };
 
-template <int J1, int J0>
+template <int NT, int J1, int J0>
 __device__ __forceinline__ void fine_adj_level(float* __restrict__ R, float* __restrict__ Ub, float* __restrict__ T,
                                                const float* __restrict__ Uc, int n, int ty0, int tx0) {
   using G = FineT<J1>;
@@ -326,14 +354,14 @@ __device__ __forceinline__ void fine_adj_level(float* __restrict__ R, float* __r
   constexpr int CI0 = (G::HX(J1) - HXi) / 4, C0 = (G::HX(J1) - HXo) / 4;
   // u_{J0-1} on the region of r_J0, loaded while this level filters
   constexpr int HRn = J0 > 0 ? G::HR(J0) : 0, HXn = J0 > 0 ? G::HX(J0) : 0;
-  Region<HRn, HXn, PA> nxt;
+  Region<NT, HRn, HXn, PA> nxt;
   if constexpr (J0 > 0) nxt.load(Uc - (size_t)n * n, n, ty0, tx0);
-  constexpr int SEGV = J0 == 0 ? 8 : (J0 == 1 ? 9 : 10);
-  vpass<D, NCHI, RO, SEGV, PA, PA, true>(R + RI0 * PA + 4 * CI0, Ub + RI0 * PA + 4 * CI0, T + 4 * CI0);
+  constexpr int SEGV = choose_seg(NT, NCHI, RO, D);
+  vpass<NT, D, NCHI, RO, SEGV, PA, PA, true>(R + RI0 * PA + 4 * CI0, Ub + RI0 * PA + 4 * CI0, T + 4 * CI0);
   __syncthreads();
-  constexpr int SEGC = NCO % 10 == 0 ? 10 : (NCO % 9 == 0 ? 9 : 8);
+  constexpr int SEGC = choose_segc(NT, RO, NCO, D);
   constexpr float inv = 1.0f / 256.0f;
-  hpass<D, RO, NCO, SEGC, C0 - CI0, PA>(T + 4 * CI0, [&](int r, int kc, float4 raw) {
+  hpass<NT, D, RO, NCO, SEGC, C0 - CI0, PA>(T + 4 * CI0, [&](int r, int kc, float4 raw) {
     const int off = (R0 + r) * PA + 4 * (C0 + kc);
     const float4 u = ld4(Ub + off);
     st4(R + off, make_float4(fmaf(raw.x, inv, u.x), fmaf(raw.y, inv, u.y), fmaf(raw.z, inv, u.z),
@@ -343,13 +371,13 @@ __device__ __forceinline__ void fine_adj_level(float* __restrict__ R, float* __r
   if constexpr (J0 > 0) {
     nxt.template store<G::HR(J1) - HRn, (G::HX(J1) - HXn) / 4>(Ub);
     __syncthreads();
-    fine_adj_level<J1, J0 - 1>(R, Ub, T, Uc - (size_t)n * n, n, ty0, tx0);
+    fine_adj_level<NT, J1, J0 - 1>(R, Ub, T, Uc - (size_t)n * n, n, ty0, tx0);
   }
 }
 
 // One tile of channel l; rin: r_J1 per channel (class-permuted, stride 2^J1),
 // channel stride rin_stride; sm: FineT<J1>::SMEM bytes.
-template <int J1>
+template <int NT, int J1>
 __device__ __forceinline__ void fine_adjoint_tile(float* __restrict__ sm, int n, int J, const float* __restrict__ rin,
                                                   size_t rin_stride, const float* __restrict__ U,
                                                   float* __restrict__ S, int l, int ty0, int tx0) {
@@ -360,7 +388,7 @@ __device__ __forceinline__ void fine_adjoint_tile(float* __restrict__ sm, int n,
   const size_t P = (size_t)n * n;
   const float* Uc = U + ((size_t)l * (J + 1) + J1 - 1) * P;   // u_{J1-1}
   {
-    Region<G::HR(J1), G::HX(J1), G::PA> ub;
+    Region<NT, G::HR(J1), G::HX(J1), G::PA> ub;
     ub.load(Uc, n, ty0, tx0);
     // r_J1 region from the class-permuted plane: per (row, class) runs of
     // sub-columns read two at a time (8-byte aligned), scattered into R
@@ -369,33 +397,46 @@ __device__ __forceinline__ void fine_adjoint_tile(float* __restrict__ sm, int n,
     const size_t mc2 = (size_t)mc * mc;
     const float* rl = rin + (size_t)l * rin_stride;
     const int sc0 = (tx0 >> J1) - HXR / SC;
-    for (int i = threadIdx.x; i < G::RA * SC * NP; i += kNT) {
-      const int cx = i % SC, rest = i / SC, p2 = rest % NP, r = rest / NP;
-      const int gy = (ty0 - G::HR(J1) + r) & m;
-      const int sc = (sc0 + 2 * p2) & mm;
-      const float2 v = __ldg(reinterpret_cast<const float2*>(rl + (size_t)((gy & (SC - 1)) * SC + cx) * mc2 +
-                                                             (size_t)(gy >> J1) * mc + sc));
-      float* d = R + r * G::PA + cx + SC * 2 * p2;
-      d[0] = v.x;
-      d[SC] = v.y;
+    constexpr int NR = G::RA * SC * NP, NRT = (NR + NT - 1) / NT;
+    float2 rv[NRT];
+#pragma unroll
+    for (int q = 0; q < NRT; ++q) {        // every load in flight before the first store
+      const int i = threadIdx.x + q * NT;
+      if (i < NR) {
+        const int cx = i % SC, rest = i / SC, p2 = rest % NP, r = rest / NP;
+        const int gy = (ty0 - G::HR(J1) + r) & m;
+        const int sc = (sc0 + 2 * p2) & mm;
+        rv[q] = __ldg(reinterpret_cast<const float2*>(rl + (size_t)((gy & (SC - 1)) * SC + cx) * mc2 +
+                                                      (size_t)(gy >> J1) * mc + sc));
+      }
+    }
+#pragma unroll
+    for (int q = 0; q < NRT; ++q) {
+      const int i = threadIdx.x + q * NT;
+      if (i < NR) {
+        const int cx = i % SC, rest = i / SC, p2 = rest % NP, r = rest / NP;
+        float* d = R + r * G::PA + cx + SC * 2 * p2;
+        d[0] = rv[q].x;
+        d[SC] = rv[q].y;
+      }
     }
     ub.template store<0, 0>(Ub);
   }
   __syncthreads();
-  fine_adj_level<J1, J1 - 1>(R, Ub, T, Uc, n, ty0, tx0);
-  for (int i = threadIdx.x; i < kT * kT / 4; i += kNT) {
+  fine_adj_level<NT, J1, J1 - 1>(R, Ub, T, Uc, n, ty0, tx0);
+  for (int i = threadIdx.x; i < kT * kT / 4; i += NT) {
     const int r = i >> 4, c = i & 15;
     st4(S + (size_t)l * P + (size_t)(ty0 + r) * n + tx0 + 4 * c,
         ld4(R + (G::HR(J1) + r) * G::PA + G::HX(J1) + 4 * c));
   }
 }
 
-template <int J1>
-__global__ void __launch_bounds__(kNT, 2)
+template <int NT, int J1>
+__global__ void __launch_bounds__(NT, 2)
 k_fine_adjoint_v(int n, int J, const float* __restrict__ rin, size_t rin_stride, const float* __restrict__ U,
                  float* __restrict__ S) {
   extern __shared__ __align__(16) float sm[];
-  fine_adjoint_tile<J1>(sm, n, J, rin, rin_stride, U, S, blockIdx.z, blockIdx.y * kT, blockIdx.x * kT);
+  fine_adjoint_tile<NT, J1>(sm, n, J, rin, rin_stride, U, S, blockIdx.z, blockIdx.y * kT, blockIdx.x * kT);
 }
 
 // ================================================================== coarse levels, one sub-image per block
@@ -411,20 +452,23 @@ template <int M, int NL> struct CoarseV {
   static constexpr size_t SMEM = (size_t)(NA + NT + (NL + 1) * NU) * sizeof(float);
 };
 
-// Outputs per work item of the coarse passes: about one item per thread
-// (M^2 / 4 chunks per pass, 256 threads), at least 2, at most 8 and at most
-// the chain length M / d.
-__host__ __device__ constexpr int coarse_seg(int M, int d) {
-  return (M * M / 1024 < 2 ? 2 : (M * M / 1024 > 8 ? 8 : M * M / 1024)) < M / d
-             ? (M * M / 1024 < 2 ? 2 : (M * M / 1024 > 8 ? 8 : M * M / 1024))
-             : M / d;
+// Chunks per work item of a periodic horizontal pass: a divisor of NCH.
+__host__ __device__ constexpr int coarse_segp(int NT, int M, int NCH, int d) {
+  int best = 1, best_cost = 1 << 30;
+  const int kr = (2 * d + 3) / 4;
+  for (int seg = 1; seg <= 8 && seg <= NCH; seg *= 2) {
+    const int items = M * (NCH / seg);
+    const int cost = ((items + NT - 1) / NT) * (2 * seg + 2 * kr);
+    if (cost <= best_cost) { best_cost = cost; best = seg; }
+  }
+  return best;
 }
 
-template <int M, int PP>
+template <int NT, int M, int PP>
 __device__ __forceinline__ void wrap_rows(float* __restrict__ A, int h, int HR) {
   // rows -h..-1 <- M-h..M-1, rows M..M+h-1 <- 0..h-1 (A points at row 0)
   constexpr int NCH = M / 4;
-  for (int i = threadIdx.x; i < 2 * h * NCH; i += kNT) {
+  for (int i = threadIdx.x; i < 2 * h * NCH; i += NT) {
     const int c = i % NCH, rr = i / NCH;
     const int dst = rr < h ? rr - h : M + rr - h;
     const int src = rr < h ? M + rr - h : rr - h;
@@ -432,18 +476,18 @@ __device__ __forceinline__ void wrap_rows(float* __restrict__ A, int h, int HR) 
   }
 }
 
-template <int M, int NL, int LV>
+template <int NT, int M, int NL, int LV>
 __device__ __forceinline__ void coarse_an(float* __restrict__ A, float* __restrict__ T, float* __restrict__ Us,
                                           float k, float rho) {
   using G = CoarseV<M, NL>;
   constexpr int d = 1 << LV, P = G::P, NCH = M / 4;
   constexpr float inv = 1.0f / 256.0f;
-  wrap_rows<M, P>(A, 2 * d, G::HR);
+  wrap_rows<NT, M, P>(A, 2 * d, G::HR);
   __syncthreads();
-  vpass<d, NCH, M, coarse_seg(M, d), P, P, false>(A - 2 * d * P, nullptr, T);
+  vpass<NT, d, NCH, M, choose_seg(NT, NCH, M, d), P, P, false>(A - 2 * d * P, nullptr, T);
   __syncthreads();
   float* Uj = Us + LV * G::NU;
-  hpass_per<d, M, NCH, coarse_seg(M, 1), P>(T, [&](int r, int kc, float4 raw) {
+  hpass_per<NT, d, M, NCH, coarse_segp(NT, M, NCH, d), P>(T, [&](int r, int kc, float4 raw) {
     float* a = A + r * P + 4 * kc;
     const float4 cn = make_float4(raw.x * inv, raw.y * inv, raw.z * inv, raw.w * inv);
     float* up = Uj + r * P + 4 * kc;
@@ -451,35 +495,35 @@ __device__ __forceinline__ void coarse_an(float* __restrict__ A, float* __restri
     st4(a, cn);
   });
   __syncthreads();
-  if constexpr (LV + 1 < NL) coarse_an<M, NL, LV + 1>(A, T, Us, k, rho);
+  if constexpr (LV + 1 < NL) coarse_an<NT, M, NL, LV + 1>(A, T, Us, k, rho);
 }
 
-template <int M, int NL, int LV>
+template <int NT, int M, int NL, int LV>
 __device__ __forceinline__ void coarse_adj(float* __restrict__ A, float* __restrict__ T, const float* __restrict__ Us) {
   using G = CoarseV<M, NL>;
   constexpr int d = 1 << LV, P = G::P, NCH = M / 4;
   constexpr float inv = 1.0f / 256.0f;
   const float* Uj = Us + LV * G::NU;
-  for (int i = threadIdx.x; i < M * NCH; i += kNT) {      // A <- r - u_j
+  for (int i = threadIdx.x; i < M * NCH; i += NT) {      // A <- r - u_j
     const int c = i % NCH, r = i / NCH;
     st4(A + r * P + 4 * c, sub4(ld4(A + r * P + 4 * c), ld4(Uj + r * P + 4 * c)));
   }
   __syncthreads();
-  wrap_rows<M, P>(A, 2 * d, G::HR);
+  wrap_rows<NT, M, P>(A, 2 * d, G::HR);
   __syncthreads();
-  vpass<d, NCH, M, coarse_seg(M, d), P, P, false>(A - 2 * d * P, nullptr, T);
+  vpass<NT, d, NCH, M, choose_seg(NT, NCH, M, d), P, P, false>(A - 2 * d * P, nullptr, T);
   __syncthreads();
-  hpass_per<d, M, NCH, coarse_seg(M, 1), P>(T, [&](int r, int kc, float4 raw) {
+  hpass_per<NT, d, M, NCH, coarse_segp(NT, M, NCH, d), P>(T, [&](int r, int kc, float4 raw) {
     const float4 u = ld4(Uj + r * P + 4 * kc);
     st4(A + r * P + 4 * kc, make_float4(fmaf(raw.x, inv, u.x), fmaf(raw.y, inv, u.y), fmaf(raw.z, inv, u.z),
                                         fmaf(raw.w, inv, u.w)));
   });
   __syncthreads();
-  if constexpr (LV > 0) coarse_adj<M, NL, LV - 1>(A, T, Us);
+  if constexpr (LV > 0) coarse_adj<NT, M, NL, LV - 1>(A, T, Us);
 }
 
 // Class sub-image cls of channel l; sm: CoarseV<M, NL>::SMEM bytes.
-template <int M, int NL>
+template <int NT, int M, int NL>
 __device__ __forceinline__ void coarse_sub(float* __restrict__ sm, int n, int J, int j1,
                                            const float* __restrict__ c_in, float* __restrict__ r_out,
                                            float* __restrict__ U, float k, float rho, int cls, int l) {
@@ -491,19 +535,36 @@ __device__ __forceinline__ void coarse_sub(float* __restrict__ sm, int n, int J,
   const size_t Pl = (size_t)n * n, sub = (size_t)cls * M * M;
   const float* src = c_in + (size_t)l * Pl + sub;
   float* Ul = U + ((size_t)l * (J + 1) + j1) * Pl + sub;
-  // the sub-image of c_j1 and of every coarse dual plane (coalesced float4)
-  for (int i = threadIdx.x; i < M * NCH; i += kNT) {
-    const int c = i % NCH, r = i / NCH;
-    st4(A + r * P + 4 * c, ldg4(src + r * M + 4 * c));
+  // the sub-image of c_j1 and of every coarse dual plane (coalesced float4),
+  // all of a thread's loads in flight before its first store
+  constexpr int NQ = (M * NCH + NT - 1) / NT;
+  float4 va[NQ], vu[NQ][NL + 1];
 #pragma unroll
-    for (int j = 0; j <= NL; ++j) st4(Us + j * G::NU + r * P + 4 * c, ldg4(Ul + (size_t)j * Pl + r * M + 4 * c));
+  for (int q = 0; q < NQ; ++q) {
+    const int i = threadIdx.x + q * NT;
+    if (i < M * NCH) {
+      const int c = i % NCH, r = i / NCH;
+      va[q] = ldg4(src + r * M + 4 * c);
+#pragma unroll
+      for (int j = 0; j <= NL; ++j) vu[q][j] = ldg4(Ul + (size_t)j * Pl + r * M + 4 * c);
+    }
+  }
+#pragma unroll
+  for (int q = 0; q < NQ; ++q) {
+    const int i = threadIdx.x + q * NT;
+    if (i < M * NCH) {
+      const int c = i % NCH, r = i / NCH;
+      st4(A + r * P + 4 * c, va[q]);
+#pragma unroll
+      for (int j = 0; j <= NL; ++j) st4(Us + j * G::NU + r * P + 4 * c, vu[q][j]);
+    }
   }
   __syncthreads();
-  coarse_an<M, NL, 0>(A, T, Us, k, rho);
+  coarse_an<NT, M, NL, 0>(A, T, Us, k, rho);
   // coarse plane: U_J <- update with c_J; r_J = U_J
   {
     float* UJ = Us + NL * G::NU;
-    for (int i = threadIdx.x; i < M * NCH; i += kNT) {
+    for (int i = threadIdx.x; i < M * NCH; i += NT) {
       const int c = i % NCH, r = i / NCH;
       const float4 nv = dual4(ld4(UJ + r * P + 4 * c), ld4(A + r * P + 4 * c), k, rho);
       st4(UJ + r * P + 4 * c, nv);
@@ -511,9 +572,9 @@ __device__ __forceinline__ void coarse_sub(float* __restrict__ sm, int n, int J,
     }
   }
   __syncthreads();
-  coarse_adj<M, NL, NL - 1>(A, T, Us);
+  coarse_adj<NT, M, NL, NL - 1>(A, T, Us);
   float* dst = r_out + (size_t)l * Pl + sub;
-  for (int i = threadIdx.x; i < M * NCH; i += kNT) {
+  for (int i = threadIdx.x; i < M * NCH; i += NT) {
     const int c = i % NCH, r = i / NCH;
     st4(dst + r * M + 4 * c, ld4(A + r * P + 4 * c));
 #pragma unroll
@@ -523,12 +584,12 @@ __device__ __forceinline__ void coarse_sub(float* __restrict__ sm, int n, int J,
 }
 
 // grid (4^j1, L): block = one class sub-image of one channel.
-template <int M, int NL>
-__global__ void __launch_bounds__(kNT, 2)
+template <int NT, int M, int NL>
+__global__ void __launch_bounds__(NT, 2)
 k_coarse_v(int n, int J, int j1, const float* __restrict__ c_in, float* __restrict__ r_out, float* __restrict__ U,
            float k, float rho) {
   extern __shared__ __align__(16) float sm[];
-  coarse_sub<M, NL>(sm, n, J, j1, c_in, r_out, U, k, rho, blockIdx.x, blockIdx.y);
+  coarse_sub<NT, M, NL>(sm, n, J, j1, c_in, r_out, U, k, rho, blockIdx.x, blockIdx.y);
 }
 
 }  // namespace vec
@@ -541,9 +602,20 @@ bool iuwt_vec_coarse_ok(const Geom& g) {
   return g.gen == 1 && g.j1 >= 1 && (M == 32 || M == 64) && NL >= 1 && NL <= 3;
 }
 
-cudaError_t launch_fine_analysis_vec(const Geom& g, const IuwtArgs& a, cudaStream_t s) {
+// Threads per block of the fine and of the coarse kernels: 256 (two blocks
+// per SM) or 512; MUFFIN_FINE_THREADS / MUFFIN_COARSE_THREADS override.
+static int vec_threads(const char* env, int dflt) {
+  const char* v = getenv(env);
+  const int t = v ? atoi(v) : dflt;
+  return t == 512 ? 512 : 256;
+}
+static int fine_threads() { static const int t = vec_threads("MUFFIN_FINE_THREADS", 256); return t; }
+static int coarse_threads_v() { static const int t = vec_threads("MUFFIN_COARSE_THREADS", 256); return t; }
+
+template <int NT>
+static cudaError_t fine_an_vec(const Geom& g, const IuwtArgs& a, cudaStream_t s) {
   dim3 grid(g.n / vec::kT, g.n / vec::kT, g.L);
-#define FA(JJ) vec::k_fine_analysis_v<JJ><<<grid, vec::kNT, vec::FineA<JJ>::SMEM, s>>>(g.n, g.J, a.D, a.U, a.cr, a.k, a.rho)
+#define FA(JJ) vec::k_fine_analysis_v<NT, JJ><<<grid, NT, vec::FineA<JJ>::SMEM, s>>>(g.n, g.J, a.D, a.U, a.cr, a.k, a.rho)
   switch (g.j1) {
     case 1: FA(1); break;
     case 2: FA(2); break;
@@ -554,13 +626,18 @@ cudaError_t launch_fine_analysis_vec(const Geom& g, const IuwtArgs& a, cudaStrea
   return cudaGetLastError();
 }
 
-cudaError_t launch_fine_adjoint_vec(const Geom& g, const IuwtArgs& a, cudaStream_t s) {
+cudaError_t launch_fine_analysis_vec(const Geom& g, const IuwtArgs& a, cudaStream_t s) {
+  return fine_threads() == 512 ? fine_an_vec<512>(g, a, s) : fine_an_vec<256>(g, a, s);
+}
+
+template <int NT>
+static cudaError_t fine_adj_vec(const Geom& g, const IuwtArgs& a, cudaStream_t s) {
   dim3 grid(g.n / vec::kT, g.n / vec::kT, g.L);
   const size_t P = (size_t)g.n * g.n;
   const bool from_u = (g.J == g.j1);
   const float* rin = from_u ? a.U + (size_t)g.J * P : a.rin;
   const size_t stride = from_u ? (size_t)(g.J + 1) * P : P;
-#define FT(JJ) vec::k_fine_adjoint_v<JJ><<<grid, vec::kNT, vec::FineT<JJ>::SMEM, s>>>(g.n, g.J, rin, stride, a.U, a.S)
+#define FT(JJ) vec::k_fine_adjoint_v<NT, JJ><<<grid, NT, vec::FineT<JJ>::SMEM, s>>>(g.n, g.J, rin, stride, a.U, a.S)
   switch (g.j1) {
     case 1: FT(1); break;
     case 2: FT(2); break;
@@ -571,29 +648,46 @@ cudaError_t launch_fine_adjoint_vec(const Geom& g, const IuwtArgs& a, cudaStream
   return cudaGetLastError();
 }
 
-cudaError_t launch_coarse_vec(const Geom& g, const float* c_in, float* r_out, float* U, float k, float rho,
+cudaError_t launch_fine_adjoint_vec(const Geom& g, const IuwtArgs& a, cudaStream_t s) {
+  return fine_threads() == 512 ? fine_adj_vec<512>(g, a, s) : fine_adj_vec<256>(g, a, s);
+}
+
+template <int NT>
+static cudaError_t coarse_vec(const Geom& g, const float* c_in, float* r_out, float* U, float k, float rho,
                               cudaStream_t s) {
   dim3 grid(1 << (2 * g.j1), g.L);
   const int M = g.n >> g.j1, NL = g.J - g.j1;
-#define CV(MM, LL)                                                                                    \
-  if (M == MM && NL == LL) {                                                                          \
-    vec::k_coarse_v<MM, LL><<<grid, vec::kNT, vec::CoarseV<MM, LL>::SMEM, s>>>(g.n, g.J, g.j1, c_in, r_out, U, k, rho); \
-    return cudaGetLastError();                                                                        \
+#define CV(MM, LL)                                                                                             \
+  if (M == MM && NL == LL) {                                                                                   \
+    vec::k_coarse_v<NT, MM, LL><<<grid, NT, vec::CoarseV<MM, LL>::SMEM, s>>>(g.n, g.J, g.j1, c_in, r_out, U, k, \
+                                                                            rho);                            \
+    return cudaGetLastError();                                                                                 \
   }
   CV(32, 1) CV(32, 2) CV(32, 3) CV(64, 1) CV(64, 2) CV(64, 3)
 #undef CV
   return cudaErrorInvalidValue;
 }
 
-cudaError_t iuwt_vec_configure() {
+cudaError_t launch_coarse_vec(const Geom& g, const float* c_in, float* r_out, float* U, float k, float rho,
+                              cudaStream_t s) {
+  return coarse_threads_v() == 512 ? coarse_vec<512>(g, c_in, r_out, U, k, rho, s)
+                                   : coarse_vec<256>(g, c_in, r_out, U, k, rho, s);
+}
+
+template <int NT> static cudaError_t vec_configure_nt() {
   cudaError_t e;
 #define SET(fn) if ((e = allow_max_dyn_smem(fn))) return e;
-  SET(vec::k_fine_analysis_v<1>) SET(vec::k_fine_analysis_v<2>) SET(vec::k_fine_analysis_v<3>)
-  SET(vec::k_fine_adjoint_v<1>) SET(vec::k_fine_adjoint_v<2>) SET(vec::k_fine_adjoint_v<3>)
-  SET((vec::k_coarse_v<32, 1>)) SET((vec::k_coarse_v<32, 2>)) SET((vec::k_coarse_v<32, 3>))
-  SET((vec::k_coarse_v<64, 1>)) SET((vec::k_coarse_v<64, 2>)) SET((vec::k_coarse_v<64, 3>))
+  SET((vec::k_fine_analysis_v<NT, 1>)) SET((vec::k_fine_analysis_v<NT, 2>)) SET((vec::k_fine_analysis_v<NT, 3>))
+  SET((vec::k_fine_adjoint_v<NT, 1>)) SET((vec::k_fine_adjoint_v<NT, 2>)) SET((vec::k_fine_adjoint_v<NT, 3>))
+  SET((vec::k_coarse_v<NT, 32, 1>)) SET((vec::k_coarse_v<NT, 32, 2>)) SET((vec::k_coarse_v<NT, 32, 3>))
+  SET((vec::k_coarse_v<NT, 64, 1>)) SET((vec::k_coarse_v<NT, 64, 2>)) SET((vec::k_coarse_v<NT, 64, 3>))
 #undef SET
   return cudaSuccess;
+}
+
+cudaError_t iuwt_vec_configure() {
+  const cudaError_t e = vec_configure_nt<256>();
+  return e != cudaSuccess ? e : vec_configure_nt<512>();
 }
 
 }  // namespace muffin

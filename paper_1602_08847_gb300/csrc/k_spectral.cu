@@ -154,7 +154,12 @@ template <int L> struct SpecTma {
   static constexpr size_t TILE = (size_t)L * 32 * sizeof(float);              // one [L][32] tile
   static constexpr size_t OFF_D = 0, OFF_V = 2 * TILE, OFF_W = 4 * TILE;       // D[2], V[2], work
   static constexpr size_t OFF_TW = OFF_W + (size_t)H * 32 * sizeof(cpx<float>);
-  static constexpr size_t OFF_BAR = OFF_TW + (size_t)H * sizeof(cpx<float>);
+  // tables, read every tile: half-length twiddles [H], twiddles, post- and pre-twiddles [L], 1/(s_k L) [L]
+  static constexpr size_t OFF_TWL = OFF_TW + (size_t)H * sizeof(cpx<float>);
+  static constexpr size_t OFF_POST = OFF_TWL + (size_t)L * sizeof(cpx<float>);
+  static constexpr size_t OFF_PRE = OFF_POST + (size_t)L * sizeof(cpx<float>);
+  static constexpr size_t OFF_INVS = OFF_PRE + (size_t)L * sizeof(cpx<float>);
+  static constexpr size_t OFF_BAR = OFF_INVS + (size_t)L * sizeof(float);
   static constexpr size_t SMEM = OFF_BAR + 64 + 128;                            // + alignment slack
 };
 
@@ -169,13 +174,25 @@ k_spectral_tma(const __grid_constant__ SpecMaps maps, SpecArgs a, int ntiles) {
   float* Vb = reinterpret_cast<float*>(sm + G::OFF_V);
   cpx<float>* work = reinterpret_cast<cpx<float>*>(sm + G::OFF_W);
   cpx<float>* twh = reinterpret_cast<cpx<float>*>(sm + G::OFF_TW);
+  cpx<float>* twl = reinterpret_cast<cpx<float>*>(sm + G::OFF_TWL);
+  cpx<float>* post = reinterpret_cast<cpx<float>*>(sm + G::OFF_POST);
+  cpx<float>* pre = reinterpret_cast<cpx<float>*>(sm + G::OFF_PRE);
+  float* invs = reinterpret_cast<float*>(sm + G::OFF_INVS);
   const uint32_t bar0 = smem_addr(sm + G::OFF_BAR);
-  const cpx<float>* twl = reinterpret_cast<const cpx<float>*>(a.tw);
-  const cpx<float>* post = reinterpret_cast<const cpx<float>*>(a.post);
-  const cpx<float>* pre = reinterpret_cast<const cpx<float>*>(a.pre);
   const int lane = threadIdx.x, t = threadIdx.y;
   const int tid = t * 32 + lane, nth = 32 * T16;
-  for (int i = tid; i < H; i += nth) twh[i] = twl[2 * i];
+  {
+    const cpx<float>* g_tw = reinterpret_cast<const cpx<float>*>(a.tw);
+    const cpx<float>* g_post = reinterpret_cast<const cpx<float>*>(a.post);
+    const cpx<float>* g_pre = reinterpret_cast<const cpx<float>*>(a.pre);
+    for (int i = tid; i < L; i += nth) {
+      twl[i] = g_tw[i];
+      post[i] = g_post[i];
+      pre[i] = g_pre[i];
+      invs[i] = a.invs[i];
+      if (i < H) twh[i] = g_tw[2 * i];
+    }
+  }
   constexpr uint32_t kBytes = 2 * (uint32_t)G::TILE;
   // thread 0: which stages have a load in flight (bit s) and its parity (bit s of pend_ph)
   uint32_t pend = 0, pend_ph = 0;
@@ -234,10 +251,10 @@ k_spectral_tma(const __grid_constant__ SpecMaps maps, SpecArgs a, int ntiles) {
 #pragma unroll
     for (int q = 0; q < 8; ++q) {
       const int k = t + q * T16;
-      const float ya = V[k * 32 + lane] * a.invs[k];
-      const float yb = k == 0 ? 0.0f : V[(L - k) * 32 + lane] * a.invs[L - k];
-      const float yc = V[(k + H) * 32 + lane] * a.invs[k + H];
-      const float yd = V[(H - k) * 32 + lane] * a.invs[H - k];
+      const float ya = V[k * 32 + lane] * invs[k];
+      const float yb = k == 0 ? 0.0f : V[(L - k) * 32 + lane] * invs[L - k];
+      const float yc = V[(k + H) * 32 + lane] * invs[k + H];
+      const float yd = V[(H - k) * 32 + lane] * invs[H - k];
       const cpx<float> w0 = mul(pre[k], mk<float>(ya, -yb));
       const cpx<float> w1 = mul(pre[k + H], mk<float>(yc, -yd));
       const cpx<float> A = add(w0, w1);

@@ -41,14 +41,18 @@ def random_state(p, seed):
     return x, u, v
 
 
-def one_pass_both(cube, p, seed, fine_levels=-1):
-    """One pass of Algorithm 1 from the same random state on both sides."""
+def one_pass_both(cube, p, seed, fine_levels=-1, n_pass=1):
+    """n_pass passes of Algorithm 1 from the same random state on both sides.
+
+    With n_pass >= 2 the second pass reads the adjoints S = W_s^T U and
+    T = W_lambda^T V that the kernels of the first pass wrote (the first pass
+    reads the ones set_state computed)."""
     x, u, v = random_state(p, seed)
     m = gpu_solver(cube, p, fine_levels)
     m.set_state(torch.from_numpy(x).cuda(), torch.from_numpy(u).cuda(), torch.from_numpy(v).cuda(), 0)
-    m.iterate(1)
+    m.iterate(n_pass)
     gx, gu, gv, _ = m.get_state()
     torch.cuda.synchronize()
     m.close()
-    s = mo.iterate(p, mo.State(x.astype(np.float64), u.astype(np.float64), v.astype(np.float64)), 1)
+    s = mo.iterate(p, mo.State(x.astype(np.float64), u.astype(np.float64), v.astype(np.float64)), n_pass)
     return (to64(gx), to64(gu), to64(gv)), s

@@ -36,11 +36,12 @@ def test_gradient_step_all_sizes(lib, n, L):
     (64, 3, 0, -1), (256, 2, 0, -1),
 ])
 def test_spatial_pass_matches_oracle(lib, gen, n, L, J, j1):
-    """mu_lambda = 0: X and every wavelet plane of U after one pass, for every
+    """mu_lambda = 0: X and every wavelet plane of U after two passes (the
+    second reads the spatial adjoint the first pass's kernels wrote), for every
     tiling split (fine halo tiles / class-permuted coarse sub-images)."""
     cube = small_cube(n, L, max(J, 1), seed=10 + n + J)
     p = problem(cube, J, gen, 0.4, 0.0, tau=None, sigma=2.0)
-    (gx, gu, gv), s = one_pass_both(cube, p, seed=5, fine_levels=j1)
+    (gx, gu, gv), s = one_pass_both(cube, p, seed=5, fine_levels=j1, n_pass=2)
     assert max_rel(gx, s.X) < TOL1
     for j in range(J + 1):
         assert max_rel(gu[:, j], s.U[:, j]) < TOL1, f"plane {j}"
@@ -49,11 +50,12 @@ def test_spatial_pass_matches_oracle(lib, gen, n, L, J, j1):
 
 @pytest.mark.parametrize("L", [1, 3, 8, 15, 16, 32, 64, 100, 128, 256])
 def test_spectral_pass_matches_oracle(lib, L):
-    """mu_s = 0: X and V after one pass (dense DCT for L not a power of two or
-    below 16, Makhoul FFT-DCT otherwise)."""
+    """mu_s = 0: X and V after two passes (dense DCT for L not a power of two or
+    below 16, Makhoul FFT-DCT otherwise; the second pass reads the T that the
+    first pass's spectral kernel wrote)."""
     cube = small_cube(16, L, 1, seed=40 + L)
     p = problem(cube, 1, 1, 0.0, 0.7, sigma=3.0)
-    (gx, gu, gv), s = one_pass_both(cube, p, seed=7)
+    (gx, gu, gv), s = one_pass_both(cube, p, seed=7, n_pass=2)
     assert max_rel(gx, s.X) < TOL1
     assert max_rel(gv, s.V) < TOL1
 
@@ -65,7 +67,7 @@ def test_full_pass_relaxed_weighted(lib, gen):
     w = np.linspace(0.5, 2.0, 6)
     # a step well inside Condat's bound so that rho = 1.3 < delta
     p = problem(cube, 3, gen, 0.3, 1.5, sigma=1.5, rho=1.3, w=w, tau=1e-3)
-    (gx, gu, gv), s = one_pass_both(cube, p, seed=9)
+    (gx, gu, gv), s = one_pass_both(cube, p, seed=9, n_pass=2)
     assert max_rel(gx, s.X) < TOL1
     assert max_rel(gu, s.U) < TOL1
     assert max_rel(gv, s.V) < TOL1
