@@ -17,50 +17,20 @@
 #include <cstdlib>
 
 #include "device.cuh"
+#include "fft_blocks.cuh"
 #include "internal.h"
 
 namespace muffin {
-
-template <int N> __host__ __device__ constexpr int rows_pairs() { return (2048 / N) < (N / 2) ? (2048 / N) : (N / 2); }
-template <int N> __host__ __device__ constexpr int cols_per_cta() { return N >= 512 ? 8 : ((N / 2) < 16 ? (N / 2) : 16); }
 
 // ------------------------------------------------------------------ FP32 rows forward
 template <int N>
 __global__ void __launch_bounds__(rows_pairs<N>() * (N / 8))
 k_rows_fwd(const float* __restrict__ X, cpx<float>* __restrict__ spec, const cpx<float>* __restrict__ twg) {
-  constexpr int T8 = N / 8, PAIRS = rows_pairs<N>(), H = N / 2, NP = fft_slots<N, 1>();
+  constexpr int PAIRS = rows_pairs<N>(), NP = fft_slots<N, 1>();
   __shared__ cpx<float> tw[N];
   __shared__ cpx<float> buf[PAIRS * NP];
-  const int f = threadIdx.x / T8, t = threadIdx.x % T8;
   for (int i = threadIdx.x; i < N; i += blockDim.x) tw[i] = twg[i];
-  const int l = blockIdx.y;
-  const int y0 = 2 * (blockIdx.x * PAIRS + f);
-  const float* r0 = X + ((size_t)l * N + y0) * N;
-  cpx<float> v[8];
-#pragma unroll
-  for (int q = 0; q < 8; ++q) v[q] = mk<float>(__ldg(r0 + t + q * T8), __ldg(r0 + N + t + q * T8));
-  __syncthreads();
-  fft_regs<float, N, -1, 1, 1>(v, buf + f * NP, tw, t);
-  __syncthreads();
-#pragma unroll
-  for (int q = 0; q < 8; ++q) buf[f * NP + fft_slot<1>(t + q * T8)] = v[q];
-  __syncthreads();
-  cpx<float>* o0 = spec + ((size_t)l * N + y0) * H;
-  cpx<float>* o1 = o0 + H;
-#pragma unroll
-  for (int q = 0; q < 4; ++q) {
-    const int k = t + q * T8;
-    const cpx<float> zk = buf[f * NP + fft_slot<1>(k)];
-    if (k == 0) {
-      const cpx<float> zn = buf[f * NP + fft_slot<1>(H)];
-      o0[0] = mk<float>(zk.x, zn.x);
-      o1[0] = mk<float>(zk.y, zn.y);
-    } else {
-      const cpx<float> zm = buf[f * NP + fft_slot<1>(N - k)];
-      o0[k] = mk<float>(0.5f * (zk.x + zm.x), 0.5f * (zk.y - zm.y));
-      o1[k] = mk<float>(0.5f * (zk.y + zm.y), 0.5f * (zm.x - zk.x));
-    }
-  }
+  rows_fwd_block<N, PAIRS>(X, spec, tw, buf, blockIdx.y, blockIdx.x);
 }
 
 // ------------------------------------------------------------------ FP32 column filter
@@ -68,44 +38,11 @@ template <int N>
 __global__ void __launch_bounds__(cols_per_cta<N>() * (N / 8))
 k_cols_filter(cpx<float>* __restrict__ spec, const float* __restrict__ Kp, const float* __restrict__ Kb,
               const cpx<float>* __restrict__ twg) {
-  constexpr int T8 = N / 8, C = cols_per_cta<N>(), H = N / 2;
   extern __shared__ __align__(16) unsigned char smraw[];
   cpx<float>* tw = reinterpret_cast<cpx<float>*>(smraw);
   cpx<float>* buf = tw + N;
-  const int c = threadIdx.x % C, t = threadIdx.x / C;
   for (int i = threadIdx.x; i < N; i += blockDim.x) tw[i] = twg[i];
-  const int l = blockIdx.y;
-  const int kx = blockIdx.x * C + c;
-  cpx<float>* base = spec + (size_t)l * N * H;
-  cpx<float> v[8];
-  float ka[8], kb[8];
-  const float* Kl = Kp + (size_t)l * N * H;
-#pragma unroll
-  for (int q = 0; q < 8; ++q) {
-    v[q] = base[(t + q * T8) * H + kx];
-    ka[q] = __ldg(Kl + (t + q * T8) * H + kx);   // multipliers arrive during the forward FFT
-    kb[q] = kx == 0 ? __ldg(Kb + (size_t)l * N + t + q * T8) : 0.0f;
-  }
-  __syncthreads();
-  fft_regs<float, N, -1, C>(v, buf + c, tw, t);
-  __syncthreads();
-#pragma unroll
-  for (int q = 0; q < 8; ++q) buf[(t + q * T8) * C + c] = v[q];
-  __syncthreads();
-#pragma unroll
-  for (int q = 0; q < 8; ++q) {
-    const int pos = t + q * T8;
-    if (kx == 0) {
-      // (DC, Nyquist) packed column: Z'(k) = a Z(k) + b conj(Z(-k))
-      const cpx<float> zm = buf[((N - pos) & (N - 1)) * C + c];
-      v[q] = add(scale(v[q], ka[q]), scale(conj(zm), kb[q]));
-    } else {
-      v[q] = scale(v[q], ka[q]);
-    }
-  }
-  fft_regs<float, N, 1, C>(v, buf + c, tw, t);
-#pragma unroll
-  for (int q = 0; q < 8; ++q) base[(t + q * T8) * H + kx] = v[q];
+  cols_block<N, cols_per_cta<N>()>(spec, Kp, Kb, tw, buf, blockIdx.y, blockIdx.x);
 }
 
 // ------------------------------------------------------------------ column filter, pipelined (TMA)
@@ -302,70 +239,11 @@ template <int N, int MODE>
 __global__ void __launch_bounds__(rows_pairs<N>() * (N / 8), 2)
 k_rows_inv(const cpx<float>* __restrict__ spec, PrimalArgs a, float* __restrict__ out,
            const cpx<float>* __restrict__ twg) {
-  constexpr int T8 = N / 8, PAIRS = rows_pairs<N>(), H = N / 2, NP = fft_slots<N, 1>();
+  constexpr int PAIRS = rows_pairs<N>(), NP = fft_slots<N, 1>();
   __shared__ cpx<float> tw[N];
   __shared__ cpx<float> buf[PAIRS * NP];
-  const int f = threadIdx.x / T8, t = threadIdx.x % T8;
   for (int i = threadIdx.x; i < N; i += blockDim.x) tw[i] = twg[i];
-  const int l = blockIdx.y;
-  const int y0 = 2 * (blockIdx.x * PAIRS + f);
-  const cpx<float>* s0 = spec + ((size_t)l * N + y0) * H;
-  const cpx<float>* s1 = s0 + H;
-  cpx<float> v[8];
-#pragma unroll
-  for (int q = 0; q < 8; ++q) {
-    const int pos = t + q * T8;
-    if (pos == 0) {
-      const cpx<float> A = s0[0], B = s1[0];
-      v[q] = mk<float>(A.x, B.x);
-    } else if (pos == H) {
-      const cpx<float> A = s0[0], B = s1[0];
-      v[q] = mk<float>(A.y, B.y);
-    } else if (pos < H) {
-      const cpx<float> A = s0[pos], B = s1[pos];
-      v[q] = mk<float>(A.x - B.y, A.y + B.x);
-    } else {
-      const cpx<float> A = s0[N - pos], B = s1[N - pos];
-      v[q] = mk<float>(A.x + B.y, B.x - A.y);
-    }
-  }
-  const size_t row0 = ((size_t)l * N + y0) * N;
-  // epilogue inputs of this thread's 16 pixels, loaded before the FFT so that
-  // their latency hides behind it: xo = X, bo = tau (mu_s S + mu_l T - b)
-  float xo[16], bo[16];
-  if constexpr (MODE == 0) {
-#pragma unroll
-    for (int q = 0; q < 8; ++q) {
-#pragma unroll
-      for (int h = 0; h < 2; ++h) {
-        const size_t idx = row0 + (size_t)h * N + t + q * T8;
-        xo[2 * q + h] = a.X[idx];
-        float st = -__ldg(a.b + idx);
-        if (a.S) st += a.mu_s * __ldg(a.S + idx);
-        if (a.T) st += a.mu_l * __ldg(a.T + idx);
-        bo[2 * q + h] = st;
-      }
-    }
-  }
-  __syncthreads();
-  fft_regs<float, N, 1, 1, 1>(v, buf + f * NP, tw, t);
-#pragma unroll
-  for (int q = 0; q < 8; ++q) {
-    const int x = t + q * T8;
-#pragma unroll
-    for (int h = 0; h < 2; ++h) {
-      const size_t idx = row0 + (size_t)h * N + x;
-      const float g = h == 0 ? v[q].x : v[q].y;
-      if constexpr (MODE == 0) {
-        const float x0 = xo[2 * q + h];
-        const float xt = fmaxf(x0 - a.tau * (g + bo[2 * q + h]), 0.0f);
-        a.D[idx] = 2.0f * xt - x0;
-        a.X[idx] = a.rho * xt + (1.0f - a.rho) * x0;
-      } else {
-        out[idx] = g;
-      }
-    }
-  }
+  rows_inv_block<N, PAIRS, MODE>(spec, a, out, tw, buf, blockIdx.y, blockIdx.x);
 }
 
 // ------------------------------------------------------------------ FP64 full complex FFT (setup, objective)

@@ -16,12 +16,12 @@
 
 #include "device.cuh"
 #include "internal.h"
+#include "spectral_blocks.cuh"
 
 namespace muffin {
 
 bool spectral_uses_fft(int L) { return L >= 16 && L <= 256 && (L & (L - 1)) == 0; }
 
-__device__ __forceinline__ int makhoul_src(int m, int L) { return m < L / 2 ? 2 * m : 2 * (L - 1 - m) + 1; }
 
 // Power-of-two L: the reordered sequence v is real, so its length-L FFT comes
 // from one length-L/2 complex FFT of z[m] = v[2m] + i v[2m+1] (even/odd

@@ -33,6 +33,7 @@ def test_gradient_step_all_sizes(lib, n, L):
     (16, 2, 3, -1), (64, 3, 3, 0), (64, 3, 3, 1), (64, 3, 3, 2), (64, 3, 3, 3), (64, 2, 5, 3),
     (128, 2, 4, 0), (128, 2, 4, 1), (128, 2, 4, 2), (256, 1, 3, 2), (256, 2, 4, -1), (256, 1, 2, -1),
     (512, 1, 5, -1), (1024, 1, 4, -1),
+    (256, 2, 4, 1), (512, 1, 5, 2), (512, 1, 4, 2), (1024, 1, 4, 3),
     (64, 3, 0, -1), (256, 2, 0, -1),
 ])
 def test_spatial_pass_matches_oracle(lib, gen, n, L, J, j1):
