@@ -407,10 +407,25 @@ def main():
         s1.record()
         torch.cuda.synchronize()
         t_seq = s0.elapsed_time(s1) / args.steps
+        # the same cubes, one persistent launch per pass
+        t_pers = None
+        try:
+            b.set_mode("persistent")
+            b.iterate(5)
+            b.check()
+            s0.record()
+            b.iterate(args.steps)
+            s1.record()
+            torch.cuda.synchronize()
+            b.check()
+            t_pers = s0.elapsed_time(s1) / args.steps
+        except Exception as exc:  # noqa: BLE001
+            t_pers = "failed: " + str(exc)[:200]
         line["batched"] = {"workload": "128^2x16 + 256^2x32 + 512^2x64 + 1024^2x8, 40 sources, 60 antennas, J=4, "
                                        "seeds 11-14, splits chosen per cube by the set-up autotuner",
                            "voxels": vox_c, "ms_per_step": t_batch, "value": vox_c / (t_batch / 1e3),
                            "unit": METRIC, "one_by_one_ms_per_step": t_seq,
+                           "persistent_ms_per_step": t_pers,
                            "tilings": [m_.tiling() for m_ in ms]}
         b.close()
         for m_ in ms:

@@ -179,6 +179,29 @@ typedef struct muffin_batch muffin_batch;
 int muffin_batch_create(muffin_batch** batch, muffin_ctx* const* ctxs, int n, cudaStream_t stream);
 int muffin_batch_iterate(muffin_batch* batch, int n_iter);
 const char* muffin_batch_last_error(const muffin_batch* batch);  /* batch may be NULL (create errors) */
+
+/* How a batch runs one pass (no change to what it computes):
+ *   mode 0  parallel branches of one CUDA graph, every cube with its own
+ *           kernels (the default);
+ *   mode 1  one persistent cooperative kernel per pass over every cube: six
+ *           stages of the pass (row FFTs, column filter, inverse rows with the
+ *           primal step, spatial analysis, coarse levels, spatial adjoint with
+ *           the spectral step), each a work list of (cube, channel, tile)
+ *           items taken by the resident blocks in turn, separated by grid
+ *           barriers.  Captured in the batch's graph like mode 0.  Needs
+ *           generation-1 IUWT cubes with N in {128, 256, 512, 1024} and a
+ *           wavelet split whose coarse sub-images are 32, 64 or 128 wide with
+ *           at most 3 coarse levels, at most 8 cubes (else MUFFIN_ERR_ARG).
+ * Every barrier wait of mode 1 gives up after a bounded number of polls
+ * (muffin_batch_set_wait_limit; polls < 0 restores the default 2^22, each
+ * poll sleeping about 128 ns): the blocks then skip the remaining stages and
+ * the launch ends; muffin_batch_check (which synchronises) reports it as
+ * MUFFIN_ERR_TIMEOUT and clears the flag.  The barrier words live in the first
+ * context's workspace. */
+int muffin_batch_set_mode(muffin_batch* batch, int mode);
+int muffin_batch_mode(const muffin_batch* batch);
+int muffin_batch_set_wait_limit(muffin_batch* batch, long long polls);
+int muffin_batch_check(muffin_batch* batch);
 void muffin_batch_destroy(muffin_batch* batch);
 
 /* Spectral l1 sum  sum_n ||W_lambda x^n||_1  of a device cube d_x [nchan][n_pix]

@@ -21,7 +21,7 @@ BUILD = os.path.join(ROOT, "_build")
 LIB = os.path.join(PKG, "libmuffin.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I", INCLUDE, "-I", CSRC]
-SOURCES = ["k_fft.cu", "k_iuwt.cu", "k_iuwt_vec.cu", "k_spectral.cu", "k_misc.cu", "muffin.cu", "k_noalloc.cu", "k_net.cu", "k_dwt.cu"]
+SOURCES = ["k_fft.cu", "k_iuwt.cu", "k_iuwt_vec.cu", "k_spectral.cu", "k_misc.cu", "muffin.cu", "k_noalloc.cu", "k_net.cu", "k_dwt.cu", "k_batch.cu"]
 
 
 def nvcc() -> str:

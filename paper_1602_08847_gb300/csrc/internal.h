@@ -131,6 +131,41 @@ cudaError_t spectral_configure(int L);
 int spectral_take_timeouts();
 cudaError_t launch_spectral(const SpecArgs& a, int npix, int L, int mode, cudaStream_t s, int* nblocks);
 
+// ---- persistent batch pass (k_batch.cu) ----
+// One cooperative launch runs one pass of Algorithm 1 over every cube of a
+// batch: six stages (row FFTs, column filter, inverse rows + primal step,
+// spatial analysis, coarse levels, spatial adjoint with the spectral step),
+// each a work list over (cube, channel, tile) items, separated by grid
+// barriers whose waits give up after `polls` polls and set *err.
+constexpr int kMaxBatchCubes = 8;
+constexpr int kBatchThreads = 512;
+struct BatchCube {
+  int n, L, J, j1;
+  int spatial, spectral;
+  float* spec;
+  const float* Kp;
+  const float* Kb;
+  const float* twf;
+  PrimalArgs pa;
+  IuwtArgs ia;
+  SpecArgs sa;
+};
+struct BatchArgs {
+  int nc;
+  BatchCube c[kMaxBatchCubes];
+  unsigned* bar;     // [0] arrivals, [1] generation; zero before each launch
+  int* err;          // set to 1 when a barrier wait gave up (sticky)
+  long long polls;
+};
+// Whether the persistent kernel has a path for this cube geometry.
+bool batch_cube_ok(const Geom& g, int spatial, int spectral);
+// Dynamic shared memory the persistent kernel needs for these cubes.
+size_t batch_smem_bytes(const BatchArgs& a);
+cudaError_t batch_configure();
+// Largest co-resident grid for smem bytes (0 if the kernel cannot run).
+int batch_grid(size_t smem);
+cudaError_t launch_batch_pass(const BatchArgs& a, size_t smem, int grid, cudaStream_t s);
+
 // ---- misc (k_misc.cu) ----
 cudaError_t launch_sum_partials(const double* partials, int n, double* out, cudaStream_t s);
 cudaError_t launch_max_partials(const double* partials, int n, double* out, cudaStream_t s);

@@ -53,7 +53,10 @@ __host__ __device__ constexpr int ceil4(int v) { return (v + 3) & ~3; }
 
 __device__ __forceinline__ float4 ld4(const float* p) { return *reinterpret_cast<const float4*>(p); }
 __device__ __forceinline__ void st4(float* p, float4 v) { *reinterpret_cast<float4*>(p) = v; }
-__device__ __forceinline__ float4 ldg4(const float* p) { return __ldg(reinterpret_cast<const float4*>(p)); }
+// Global loads at L2 (ld.global.cg): coherent with what other blocks of the same
+// launch wrote before a grid barrier (the persistent batch kernel), and these
+// streams gain nothing from L1.
+__device__ __forceinline__ float4 ldg4(const float* p) { return __ldcg(reinterpret_cast<const float4*>(p)); }
 __device__ __forceinline__ float4 sub4(float4 a, float4 b) { return make_float4(a.x - b.x, a.y - b.y, a.z - b.z, a.w - b.w); }
 __device__ __forceinline__ float comp(const float4& v, int e) { return e == 0 ? v.x : e == 1 ? v.y : e == 2 ? v.z : v.w; }
 __device__ __forceinline__ float& compr(float4& v, int e) { return e == 0 ? v.x : e == 1 ? v.y : e == 2 ? v.z : v.w; }
@@ -404,7 +407,7 @@ __device__ __forceinline__ void fine_adjoint_tile(float* __restrict__ sm, int n,
         const int cx = i % SC, rest = i / SC, p2 = rest % NP, r = rest / NP;
         const int gy = (ty0 - G::HR(J1) + r) & m;
         const int sc = (sc0 + 2 * p2) & mm;
-        rv[q] = __ldg(reinterpret_cast<const float2*>(rl + (size_t)((gy & (SC - 1)) * SC + cx) * mc2 +
+        rv[q] = __ldcg(reinterpret_cast<const float2*>(rl + (size_t)((gy & (SC - 1)) * SC + cx) * mc2 +
                                                       (size_t)(gy >> J1) * mc + sc));
       }
     }

@@ -985,10 +985,84 @@ struct muffin_batch {
   cudaEvent_t fork = nullptr;
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t exec = nullptr;
+  int mode = 0;                 // 0: graph branches, 1: one persistent launch per pass
+  long long polls = 1LL << 22;  // bound of the persistent kernel's barrier waits
   std::string err;
 };
 
-static int bfail(muffin_batch* b, int code, const char* what, const char* detail = nullptr) {
+static int bfail(muffin_batch* b, int code, const char* what, const char* detail = nullptr);
+
+// Arguments of one cube for the persistent batch kernel (the pass of enqueue_pass, whole cube).
+static void batch_cube_of(const muffin_ctx* ctx, BatchCube* c) {
+  const Geom& g = ctx->g;
+  const Layout& lo = ctx->lo;
+  const bool spatial = ctx->mu_s != 0.0, spectral = ctx->mu_l != 0.0;
+  *c = BatchCube{};
+  c->n = g.n; c->L = g.L; c->J = g.J; c->j1 = g.j1;
+  c->spatial = spatial ? 1 : 0;
+  c->spectral = spectral ? 1 : 0;
+  c->spec = ctx->at<float>(lo.spec);
+  c->Kp = ctx->at<float>(lo.Kp);
+  c->Kb = ctx->at<float>(lo.Kb);
+  c->twf = ctx->at<float>(lo.twf);
+  PrimalArgs& pa = c->pa;
+  pa.b = ctx->at<float>(lo.b);
+  pa.S = spatial ? ctx->at<float>(lo.S) : nullptr;
+  pa.T = spectral ? ctx->at<float>(lo.T) : nullptr;
+  pa.X = ctx->X();
+  pa.D = ctx->at<float>(lo.D);
+  pa.tau = (float)ctx->tau;
+  pa.mu_s = (float)ctx->mu_s;
+  pa.mu_l = (float)ctx->mu_l;
+  pa.rho = (float)ctx->rho;
+  IuwtArgs& ia = c->ia;
+  ia.D = ctx->at<float>(lo.D);
+  ia.U = ctx->U();
+  ia.cr = ctx->at<float>(lo.cr);
+  ia.rin = ctx->at<float>(lo.cr);
+  ia.S = ctx->at<float>(lo.S);
+  ia.k = (float)(ctx->sigma * ctx->mu_s);
+  ia.rho = (float)ctx->rho;
+  SpecArgs& sa = c->sa;
+  sa.D = ctx->at<float>(lo.D);
+  sa.V = ctx->V();
+  sa.T = ctx->at<float>(lo.T);
+  sa.k = (float)(ctx->sigma * ctx->mu_l);
+  sa.rho = (float)ctx->rho;
+  sa.tw = ctx->at<float>(lo.twL);
+  sa.post = ctx->at<float>(lo.post);
+  sa.pre = ctx->at<float>(lo.pre);
+  sa.invs = ctx->at<float>(lo.invs);
+  sa.dense = ctx->at<float>(lo.dense);
+}
+
+// The barrier words and the error word of the persistent kernel live in the
+// first context's scalar area (doubles 48 and 49).
+static unsigned* batch_bar(const muffin_batch* b) { return reinterpret_cast<unsigned*>(b->ctx[0]->scal() + 48); }
+static int* batch_errw(const muffin_batch* b) { return reinterpret_cast<int*>(b->ctx[0]->scal() + 49); }
+
+static int batch_args(muffin_batch* b, BatchArgs* a, size_t* smem, int* grid) {
+  if ((int)b->ctx.size() > kMaxBatchCubes) return bfail(b, MUFFIN_ERR_ARG, "the persistent batch takes at most 8 cubes");
+  *a = BatchArgs{};
+  a->nc = (int)b->ctx.size();
+  for (int i = 0; i < a->nc; ++i) {
+    const muffin_ctx* c = b->ctx[i];
+    if (!batch_cube_ok(c->g, c->mu_s != 0.0, c->mu_l != 0.0))
+      return bfail(b, MUFFIN_ERR_ARG, "a cube of the batch has no path in the persistent kernel",
+                   "generation 1 IUWT, N in {128, 256, 512, 1024}, wavelet split 1..3 with coarse sub-images of "
+                   "32, 64 or 128 and at most 3 coarse levels");
+    batch_cube_of(c, &a->c[i]);
+  }
+  a->bar = batch_bar(b);
+  a->err = batch_errw(b);
+  a->polls = b->polls;
+  *smem = batch_smem_bytes(*a);
+  *grid = batch_grid(*smem);
+  if (*grid <= 0) return bfail(b, MUFFIN_ERR_ARG, "the persistent batch kernel does not fit on this device");
+  return MUFFIN_OK;
+}
+
+static int bfail(muffin_batch* b, int code, const char* what, const char* detail) {
   std::string m = what;
   if (detail) { m += ": "; m += detail; }
   if (b) b->err = m; else g_init_error = m;
@@ -1008,9 +1082,30 @@ static void batch_drop_graph(muffin_batch* b) {
   b->graph = nullptr;
 }
 
-// One pass of every cube as parallel branches of one graph.
+// One pass of every cube: parallel branches of one graph (mode 0), or one
+// persistent cooperative launch (mode 1) after clearing its barrier words.
 static int batch_capture(muffin_batch* b) {
   batch_drop_graph(b);
+  if (b->mode == 1) {
+    BatchArgs a;
+    size_t smem = 0;
+    int grid = 0;
+    const int r = batch_args(b, &a, &smem, &grid);
+    if (r != MUFFIN_OK) return r;
+    BCK(cudaStreamBeginCapture(b->cap, cudaStreamCaptureModeThreadLocal));
+    cudaError_t e = cudaMemsetAsync(a.bar, 0, 2 * sizeof(unsigned), b->cap);
+    if (e == cudaSuccess) e = launch_batch_pass(a, smem, grid, b->cap);
+    cudaGraph_t gr = nullptr;
+    const cudaError_t e2 = cudaStreamEndCapture(b->cap, &gr);
+    if (e != cudaSuccess || e2 != cudaSuccess) {
+      if (gr) cudaGraphDestroy(gr);
+      return bfail(b, MUFFIN_ERR_CUDA, "capture of the persistent batch pass", cudaGetErrorString(e != cudaSuccess ? e : e2));
+    }
+    b->graph = gr;
+    BCK(cudaGraphInstantiate(&b->exec, b->graph, 0));
+    for (size_t i = 0; i < b->ctx.size(); ++i) b->version[i] = b->ctx[i]->version;
+    return MUFFIN_OK;
+  }
   BCK(cudaStreamBeginCapture(b->cap, cudaStreamCaptureModeThreadLocal));
   int r = MUFFIN_OK;
   std::string why;
@@ -1078,6 +1173,49 @@ int muffin_batch_iterate(muffin_batch* b, int n_iter) {
   }
   for (int i = 0; i < n_iter; ++i) BCK(cudaGraphLaunch(b->exec, b->stream));
   for (muffin_ctx* c : b->ctx) c->iter += n_iter;
+  return MUFFIN_OK;
+}
+
+int muffin_batch_set_mode(muffin_batch* b, int mode) {
+  if (!b) return bfail(nullptr, MUFFIN_ERR_ARG, "batch is NULL");
+  if (mode != 0 && mode != 1) return bfail(b, MUFFIN_ERR_ARG, "mode must be 0 (graph branches) or 1 (persistent launch)");
+  if (mode == 1) {
+    cudaError_t e = batch_configure();
+    if (e != cudaSuccess) return bfail(b, MUFFIN_ERR_CUDA, "persistent batch kernel", cudaGetErrorString(e));
+    BatchArgs a;
+    size_t smem = 0;
+    int grid = 0;
+    const int r = batch_args(b, &a, &smem, &grid);
+    if (r != MUFFIN_OK) return r;
+    // clear the error word once (it is sticky until muffin_batch_check)
+    BCK(cudaMemsetAsync(batch_errw(b), 0, sizeof(int), b->stream));
+  }
+  b->mode = mode;
+  batch_drop_graph(b);
+  return MUFFIN_OK;
+}
+
+int muffin_batch_mode(const muffin_batch* b) { return b ? b->mode : -1; }
+
+int muffin_batch_set_wait_limit(muffin_batch* b, long long polls) {
+  if (!b) return bfail(nullptr, MUFFIN_ERR_ARG, "batch is NULL");
+  b->polls = polls < 0 ? (1LL << 22) : polls;
+  batch_drop_graph(b);
+  return MUFFIN_OK;
+}
+
+int muffin_batch_check(muffin_batch* b) {
+  if (!b) return bfail(nullptr, MUFFIN_ERR_ARG, "batch is NULL");
+  BCK(cudaStreamSynchronize(b->stream));
+  if (b->mode != 1) return MUFFIN_OK;
+  int h = 0;
+  BCK(cudaMemcpy(&h, batch_errw(b), sizeof(int), cudaMemcpyDeviceToHost));
+  if (h != 0) {
+    BCK(cudaMemset(batch_errw(b), 0, sizeof(int)));
+    return bfail(b, MUFFIN_ERR_TIMEOUT,
+                 "a grid barrier of the persistent batch pass gave up its bounded wait; the blocks skipped the "
+                 "remaining stages, so the state of the batch's cubes is incomplete");
+  }
   return MUFFIN_OK;
 }
 

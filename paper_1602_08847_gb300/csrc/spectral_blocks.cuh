@@ -3,6 +3,7 @@
 // handles NT / (2L) tiles of 32 pixels at once (thread group g = tid / (2L)
 // takes tile tile0 + g), each as in k_spectral_fft (Makhoul's DCT through a
 // half-length complex FFT, pixels on lanes).  Power-of-two L with 2L <= NT.
+// D is read at L2 (__ldcg): it is written earlier in the same launch.
 #pragma once
 #include "device.cuh"
 #include "internal.h"
@@ -41,8 +42,8 @@ __device__ __forceinline__ void spectral_update_block(const SpecArgs& a, int npi
 #pragma unroll
   for (int q = 0; q < 8; ++q) {
     const int m = t + q * T16;
-    z[q] = ok ? mk<float>(__ldg(a.D + (size_t)makhoul_src(2 * m, L) * P + pix),
-                          __ldg(a.D + (size_t)makhoul_src(2 * m + 1, L) * P + pix))
+    z[q] = ok ? mk<float>(__ldcg(a.D + (size_t)makhoul_src(2 * m, L) * P + pix),
+                          __ldcg(a.D + (size_t)makhoul_src(2 * m + 1, L) * P + pix))
               : mk<float>(0.0f, 0.0f);
   }
   __syncthreads();
@@ -110,7 +111,7 @@ __device__ __forceinline__ void spectral_dense_block(const SpecArgs& a, int npix
   const int pix = tile * 32 + lane;
   const bool ok = pix < npix;
   const size_t P = (size_t)npix;
-  for (int l = w; l < L; l += W) db[l * 32 + lane] = ok ? __ldg(a.D + (size_t)l * P + pix) : 0.0f;
+  for (int l = w; l < L; l += W) db[l * 32 + lane] = ok ? __ldcg(a.D + (size_t)l * P + pix) : 0.0f;
   __syncthreads();
   for (int kk = w; kk < L; kk += W) {
     const float* row = a.dense + (size_t)kk * L;

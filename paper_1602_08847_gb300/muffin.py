@@ -68,6 +68,10 @@ def _load():
         "muffin_batch_create": (I, [ctypes.POINTER(P), ctypes.POINTER(P), I, P]),
         "muffin_batch_iterate": (I, [P, I]),
         "muffin_batch_last_error": (ctypes.c_char_p, [P]),
+        "muffin_batch_set_mode": (I, [P, I]),
+        "muffin_batch_mode": (I, [P]),
+        "muffin_batch_set_wait_limit": (I, [P, ctypes.c_longlong]),
+        "muffin_batch_check": (I, [P]),
         "muffin_batch_destroy": (V, [P]),
         "muffin_destroy": (V, [P]),
     }
@@ -264,6 +268,29 @@ class Batch:
 
     def iterate(self, n: int = 1):
         r = _lib.muffin_batch_iterate(self._b, int(n))
+        if r != MUFFIN_OK:
+            raise MuffinError(r, _lib.muffin_batch_last_error(self._b).decode())
+
+    def set_mode(self, mode: str):
+        """"graph": parallel graph branches per cube; "persistent": one persistent launch per pass."""
+        m = {"graph": 0, "persistent": 1}[mode]
+        r = _lib.muffin_batch_set_mode(self._b, m)
+        if r != MUFFIN_OK:
+            raise MuffinError(r, _lib.muffin_batch_last_error(self._b).decode())
+
+    @property
+    def mode(self) -> str:
+        return {0: "graph", 1: "persistent"}[int(_lib.muffin_batch_mode(self._b))]
+
+    def set_wait_limit(self, polls: int | None):
+        """Poll bound of the persistent kernel's barrier waits (None: the default)."""
+        r = _lib.muffin_batch_set_wait_limit(self._b, -1 if polls is None else int(polls))
+        if r != MUFFIN_OK:
+            raise MuffinError(r, _lib.muffin_batch_last_error(self._b).decode())
+
+    def check(self):
+        """Wait for the batch; raise MuffinError(TIMEOUT) if a barrier wait gave up."""
+        r = _lib.muffin_batch_check(self._b)
         if r != MUFFIN_OK:
             raise MuffinError(r, _lib.muffin_batch_last_error(self._b).decode())
 
