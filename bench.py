@@ -41,6 +41,8 @@ def parse():
     ap.add_argument("--no-ttt", action="store_true")
     ap.add_argument("--no-batch", action="store_true")
     ap.add_argument("--no-union", action="store_true")
+    ap.add_argument("--ttt-seeds", type=int, default=0,
+                    help="also rerun the warm-start evaluation live on this many held-out seeds (5000 ...)")
     ap.add_argument("--fine-levels", type=int, default=-1,
                     help="wavelet split (levels on halo tiles); -1: chosen by timing at set-up")
     return ap.parse_args()
@@ -294,6 +296,7 @@ def main():
     value = replicas.aggregate_throughput(voxels * args.steps, world, ms / 1e3)
     launches = m.kernels_per_iteration() * args.steps
     fine_levels, cluster = m.tiling()
+    fine_threads, coarse_threads = m.block_threads()
 
     # per-stage device times over a second timed region (events between stages on the launching stream)
     names = [s for s in __import__("paper_1602_08847_gb300.muffin", fromlist=["stage_names"]).stage_names()]
@@ -333,7 +336,8 @@ def main():
             "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {"workload": WORKLOAD, "voxels_per_gpu": voxels, "nscales": J, "iuwt_gen": 1,
                        "l2": "inputs larger than L2 (state ~2.4 GB per cube)", "parallelism": f"replicas{world}",
-                       "graph": True, "iuwt_fine_levels": fine_levels, "iuwt_cluster": cluster},
+                       "graph": True, "iuwt_fine_levels": fine_levels, "iuwt_cluster": cluster,
+                       "iuwt_block_threads": [fine_threads, coarse_threads]},
             "roofline": roofline, "gpu_launches": launches, "clocks": clk.summary()}
 
     # end to end through the public call: pinned host cubes in, X back to host
@@ -446,6 +450,17 @@ def main():
             ttt["warm"] = r["net"]
             ttt["warm"]["input_passes"] = meta.get("input_passes", 0)
             ttt["warm_over_zero_gpu_ms"] = (r["net"]["pass_ms"] + r["net"]["start_ms"]) / r["zero"]["pass_ms"]
+            if meta.get("eval"):
+                ttt["held_out_record"] = {"seeds": meta.get("eval_seeds"), "summary": meta["eval"],
+                                          "what": "evaluation in the committed training record "
+                                                  "(paper_1602_08847_gb300/weights/warmstart_256x256x64.json)",
+                                          "command": meta.get("command")}
+            if args.ttt_seeds > 0:
+                live = []
+                for seed in range(5000, 5000 + args.ttt_seeds):
+                    _, y_s, h_s = synth.cube_arrays(("256x256x64", seed))
+                    live.append(ws.evaluate_one(net, y_s, h_s, 4, input_passes=meta.get("input_passes", 0)))
+                ttt["held_out_live"] = {"seeds": f"5000:{5000 + args.ttt_seeds}", "summary": ws.summarise(live)}
             net.close()
         line["time_to_rel_obj_1e-4"] = ttt
 

@@ -159,6 +159,12 @@ int muffin_plan(const muffin_ctx* ctx, int* channels_per_group, int* branches);
  * kernel).  Either pointer may be NULL. */
 int muffin_tiling(const muffin_ctx* ctx, int* fine_levels, int* cluster);
 
+/* Threads per block of the vectorised wavelet kernels of the split in use
+ * (256 or 512; each block size has its own work runs per thread), chosen by
+ * the set-up autotuner with the split when fine_levels < 0.  Either pointer
+ * may be NULL. */
+int muffin_block_threads(const muffin_ctx* ctx, int* fine_threads, int* coarse_threads);
+
 const char* muffin_last_error(const muffin_ctx* ctx);  /* ctx may be NULL (init errors) */
 
 /* The Daubechies lowpass filter with p vanishing moments (1 <= p <= 8) that

@@ -16,6 +16,8 @@ struct Geom {
   int cs;       // blocks per cluster of the coarse kernel (0: single-block streaming kernel)
   int dict = 0; // W_s: 0 IUWT, 1 union of eight Daubechies bases (k_dwt.cu)
   int vec = 1;  // generation 1: the vectorised pass kernels (k_iuwt_vec.cu) where the geometry allows
+  int fnt = 256;  // threads per block of the vectorised fine kernels (256 or 512)
+  int cnt = 256;  // threads per block of the vectorised resident coarse kernel (256 or 512)
 };
 
 // ---- FFT path (k_fft.cu) ----

@@ -1059,6 +1059,9 @@ template <int GEN> static cudaError_t cfg_gen(Geom& g) {
 cudaError_t iuwt_configure(Geom& g) {
   // MUFFIN_IUWT_GENERAL: the general kernels for every generation (comparisons)
   g.vec = (g.gen == 1 && getenv("MUFFIN_IUWT_GENERAL") == nullptr) ? 1 : 0;
+  // MUFFIN_FINE_THREADS / MUFFIN_COARSE_THREADS (256 or 512) fix the block sizes the autotuner would choose
+  if (const char* v = getenv("MUFFIN_FINE_THREADS")) g.fnt = atoi(v) == 512 ? 512 : 256;
+  if (const char* v = getenv("MUFFIN_COARSE_THREADS")) g.cnt = atoi(v) == 512 ? 512 : 256;
   if (g.vec) {
     const cudaError_t e = iuwt_vec_configure();
     if (e != cudaSuccess) return e;

@@ -14,15 +14,8 @@ bool iuwt_vec_coarse_ok(const Geom& g) {
   return g.gen == 1 && g.j1 >= 1 && (M == 32 || M == 64 || M == 128) && NL >= 1 && NL <= 3;
 }
 
-// Threads per block of the fine and of the coarse kernels: 256 (two blocks
-// per SM) or 512; MUFFIN_FINE_THREADS / MUFFIN_COARSE_THREADS override.
-static int vec_threads(const char* env, int dflt) {
-  const char* v = getenv(env);
-  const int t = v ? atoi(v) : dflt;
-  return t == 512 ? 512 : 256;
-}
-static int fine_threads() { static const int t = vec_threads("MUFFIN_FINE_THREADS", 256); return t; }
-static int coarse_threads_v() { static const int t = vec_threads("MUFFIN_COARSE_THREADS", 256); return t; }
+// Threads per block of the fine and of the coarse kernels: g.fnt / g.cnt,
+// 256 (two blocks per SM) or 512, chosen by the set-up autotuner.
 
 template <int NT>
 static cudaError_t fine_an_vec(const Geom& g, const IuwtArgs& a, cudaStream_t s) {
@@ -39,7 +32,7 @@ static cudaError_t fine_an_vec(const Geom& g, const IuwtArgs& a, cudaStream_t s)
 }
 
 cudaError_t launch_fine_analysis_vec(const Geom& g, const IuwtArgs& a, cudaStream_t s) {
-  return fine_threads() == 512 ? fine_an_vec<512>(g, a, s) : fine_an_vec<256>(g, a, s);
+  return g.fnt == 512 ? fine_an_vec<512>(g, a, s) : fine_an_vec<256>(g, a, s);
 }
 
 template <int NT>
@@ -61,7 +54,7 @@ static cudaError_t fine_adj_vec(const Geom& g, const IuwtArgs& a, cudaStream_t s
 }
 
 cudaError_t launch_fine_adjoint_vec(const Geom& g, const IuwtArgs& a, cudaStream_t s) {
-  return fine_threads() == 512 ? fine_adj_vec<512>(g, a, s) : fine_adj_vec<256>(g, a, s);
+  return g.fnt == 512 ? fine_adj_vec<512>(g, a, s) : fine_adj_vec<256>(g, a, s);
 }
 
 template <int NT>
@@ -91,7 +84,7 @@ static cudaError_t coarse_vec(const Geom& g, const float* c_in, float* r_out, fl
 
 cudaError_t launch_coarse_vec(const Geom& g, const float* c_in, float* r_out, float* U, float k, float rho,
                               cudaStream_t s) {
-  return coarse_threads_v() == 512 ? coarse_vec<512>(g, c_in, r_out, U, k, rho, s)
+  return g.cnt == 512 ? coarse_vec<512>(g, c_in, r_out, U, k, rho, s)
                                    : coarse_vec<256>(g, c_in, r_out, U, k, rho, s);
 }
 

@@ -494,6 +494,22 @@ static int autotune_split(muffin_ctx* ctx) {
     if (r != MUFFIN_OK) return r;
     if (!any || ms < best) { best = ms; best_g = g; any = true; }
   }
+  // then the block shapes of the vectorised kernels for that split: 256 or 512 threads
+  // (different work runs per thread), fine and coarse kernels each
+  if (any && best_g.vec && getenv("MUFFIN_FINE_THREADS") == nullptr && getenv("MUFFIN_COARSE_THREADS") == nullptr) {
+    for (int fnt : {256, 512}) {
+      for (int cnt : {256, 512}) {
+        if (fnt == best_g.fnt && cnt == best_g.cnt) continue;
+        Geom g = best_g;
+        g.fnt = fnt;
+        g.cnt = cnt;
+        float ms = 0.0f;
+        const int r = time_split(ctx, g, &ms);
+        if (r != MUFFIN_OK) return r;
+        if (ms < best) { best = ms; best_g = g; }
+      }
+    }
+  }
   if (any) ctx->g = best_g;
   cudaError_t e = iuwt_configure(ctx->g);
   if (e != cudaSuccess) return fail(ctx, MUFFIN_ERR_CUDA, "wavelet configuration", cudaGetErrorString(e));
@@ -952,6 +968,13 @@ int muffin_plan(const muffin_ctx* ctx, int* channels_per_group, int* branches) {
   pass_plan(ctx, false, &G, &ngroups, &nb);
   if (channels_per_group) *channels_per_group = G;
   if (branches) *branches = nb;
+  return MUFFIN_OK;
+}
+
+int muffin_block_threads(const muffin_ctx* ctx, int* fine_threads, int* coarse_threads) {
+  if (!ctx) return MUFFIN_ERR_ARG;
+  if (fine_threads) *fine_threads = ctx->g.fnt;
+  if (coarse_threads) *coarse_threads = ctx->g.cnt;
   return MUFFIN_OK;
 }
 

@@ -57,6 +57,7 @@ def _load():
         "muffin_step_sizes": (I, [P, pd, pd, pd, pd, pd, pd, pd]),
         "muffin_iterate_timed": (I, [P, I, pd, I]),
         "muffin_set_plan": (I, [P, I, I]),
+        "muffin_block_threads": (I, [P, ctypes.POINTER(I), ctypes.POINTER(I)]),
         "muffin_plan": (I, [P, ctypes.POINTER(I), ctypes.POINTER(I)]),
         "muffin_num_stages": (I, []),
         "muffin_stage_name": (ctypes.c_char_p, [I]),
@@ -235,6 +236,12 @@ class Muffin:
         g, b = ctypes.c_int(), ctypes.c_int()
         self._check(_lib.muffin_plan(self._ctx, ctypes.byref(g), ctypes.byref(b)))
         return g.value, b.value
+
+    def block_threads(self) -> tuple[int, int]:
+        """Threads per block of the vectorised fine and coarse wavelet kernels."""
+        f, c = ctypes.c_int(), ctypes.c_int()
+        self._check(_lib.muffin_block_threads(self._ctx, ctypes.byref(f), ctypes.byref(c)))
+        return f.value, c.value
 
     def tiling(self) -> tuple[int, int]:
         j1, cs = ctypes.c_int(), ctypes.c_int()

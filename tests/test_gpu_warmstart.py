@@ -60,3 +60,22 @@ def test_rejected_prediction_leaves_the_state_alone(committed):
     assert torch.equal(x0, x1) and torch.equal(u0, u1) and torch.equal(v0, v1)
     m.close()
     bad.close()
+
+
+def test_held_out_evaluation(committed):
+    """The evaluation of the training record, rerun on held-out seeds 5000 ..
+    5000 + n - 1 (n = MUFFIN_WARMSTART_SEEDS; about 1.5 s of GPU time per cube,
+    so it runs only when asked): every cube reaches the tolerance from both
+    starts, and the network's start takes less GPU time on the median cube."""
+    n = int(os.environ.get("MUFFIN_WARMSTART_SEEDS", "0"))
+    if n <= 0:
+        pytest.skip("set MUFFIN_WARMSTART_SEEDS (e.g. 200) to rerun the held-out evaluation")
+    ws, net, meta = committed
+    results = []
+    for seed in range(5000, 5000 + n):
+        _, y, h = synth.cube_arrays(("256x256x64", seed))
+        results.append(ws.evaluate_one(net, y, h, 4, input_passes=meta["input_passes"]))
+    s = ws.summarise(results)
+    print(s)
+    assert s["zero"]["reached"] == n and s["net"]["reached"] == n
+    assert s["net"]["gpu_ms_median"] < s["zero"]["gpu_ms_median"], s
