@@ -107,6 +107,26 @@ __device__ __forceinline__ void vpass(const float* __restrict__ in, const float*
   }
 }
 
+// Unnormalised B3 sums of the four lanes of the chunk at window index k0:
+// lane e takes input columns 4 k0 + e + t D, t = -2..2 (register picks fixed
+// at compile time).
+template <int D, int NW>
+__device__ __forceinline__ float4 hsum(const float4 (&w)[NW], int k0) {
+  float4 o;
+#pragma unroll
+  for (int e = 0; e < 4; ++e) {
+    float tap[5];
+#pragma unroll
+    for (int t = 0; t < 5; ++t) {
+      const int off = e + (t - 2) * D;                         // column offset from chunk start
+      const int dk = off >= 0 ? off / 4 : -((-off + 3) / 4);   // floor(off / 4)
+      tap[t] = comp(w[k0 + dk], off - 4 * dk);
+    }
+    compr(o, e) = b3u(tap[0], tap[1], tap[2], tap[3], tap[4]);
+  }
+  return o;
+}
+
 // ------------------------------------------------------------------ horizontal pass
 // Output chunk k (0 <= k < NCO) of row r (0 <= r < NR): lane e is the
 // unnormalised B3 sum of input columns 4 (k + KO) + e + t D, t = -2..2, where
@@ -129,23 +149,8 @@ __device__ __forceinline__ void hpass(const float* __restrict__ in, F&& epi) {
     for (int q = 0; q < NW; ++q)
       if (k0 + q - KR < NCO + KR) w[q] = ld4(row + 4 * q);
 #pragma unroll
-    for (int i = 0; i < SEGC; ++i) {
-      if (k0 + i < NCO) {
-        float4 o;
-#pragma unroll
-        for (int e = 0; e < 4; ++e) {
-          float tap[5];
-#pragma unroll
-          for (int t = 0; t < 5; ++t) {
-            const int off = e + (t - 2) * D;                         // column offset from chunk start
-            const int dk = off >= 0 ? off / 4 : -((-off + 3) / 4);   // floor(off / 4)
-            tap[t] = comp(w[i + KR + dk], off - 4 * dk);
-          }
-          compr(o, e) = b3u(tap[0], tap[1], tap[2], tap[3], tap[4]);
-        }
-        epi(r, k0 + i, o);
-      }
-    }
+    for (int i = 0; i < SEGC; ++i)
+      if (k0 + i < NCO) epi(r, k0 + i, hsum<D>(w, i + KR));
   }
 }
 
@@ -167,21 +172,7 @@ __device__ __forceinline__ void hpass_per(const float* __restrict__ in, F&& epi)
 #pragma unroll
     for (int q = 0; q < NW; ++q) w[q] = ld4(row + 4 * ((k0 + q - KR + NCH) % NCH));
 #pragma unroll
-    for (int i = 0; i < SEGC; ++i) {
-      float4 o;
-#pragma unroll
-      for (int e = 0; e < 4; ++e) {
-        float tap[5];
-#pragma unroll
-        for (int t = 0; t < 5; ++t) {
-          const int off = e + (t - 2) * D;
-          const int dk = off >= 0 ? off / 4 : -((-off + 3) / 4);
-          tap[t] = comp(w[i + KR + dk], off - 4 * dk);
-        }
-        compr(o, e) = b3u(tap[0], tap[1], tap[2], tap[3], tap[4]);
-      }
-      epi(r, k0 + i, o);
-    }
+    for (int i = 0; i < SEGC; ++i) epi(r, k0 + i, hsum<D>(w, i + KR));
   }
 }
 
@@ -499,25 +490,27 @@ __device__ __forceinline__ void coarse_an(float* __restrict__ A, float* __restri
   if constexpr (LV + 1 < NL) coarse_an<NT, M, NL, LV + 1>(A, T, Us, k, rho);
 }
 
+// On entry A holds r_{LV+1} - u_LV (the difference is formed in the previous
+// level's epilogue, not in a separate pass); leaves r_LV - u_{LV-1} (LV > 0)
+// or r_LV (LV = 0) in A.
 template <int NT, int M, int NL, int LV>
 __device__ __forceinline__ void coarse_adj(float* __restrict__ A, float* __restrict__ T, const float* __restrict__ Us) {
   using G = CoarseV<M, NL>;
   constexpr int d = 1 << LV, P = G::P, NCH = M / 4;
   constexpr float inv = 1.0f / 256.0f;
   const float* Uj = Us + LV * G::NU;
-  for (int i = threadIdx.x; i < M * NCH; i += NT) {      // A <- r - u_j
-    const int c = i % NCH, r = i / NCH;
-    st4(A + r * P + 4 * c, sub4(ld4(A + r * P + 4 * c), ld4(Uj + r * P + 4 * c)));
-  }
-  __syncthreads();
   wrap_rows<NT, M, P>(A, 2 * d, G::HR);
   __syncthreads();
   vpass<NT, d, NCH, M, choose_seg(NT, NCH, M, d), P, P, false>(A - 2 * d * P, nullptr, T);
   __syncthreads();
   hpass_per<NT, d, M, NCH, coarse_segp(NT, M, NCH, d), P>(T, [&](int r, int kc, float4 raw) {
     const float4 u = ld4(Uj + r * P + 4 * kc);
-    st4(A + r * P + 4 * kc, make_float4(fmaf(raw.x, inv, u.x), fmaf(raw.y, inv, u.y), fmaf(raw.z, inv, u.z),
-                                        fmaf(raw.w, inv, u.w)));
+    const float4 rj = make_float4(fmaf(raw.x, inv, u.x), fmaf(raw.y, inv, u.y), fmaf(raw.z, inv, u.z),
+                                  fmaf(raw.w, inv, u.w));
+    if constexpr (LV > 0)
+      st4(A + r * P + 4 * kc, sub4(rj, ld4(Uj - G::NU + r * P + 4 * kc)));
+    else
+      st4(A + r * P + 4 * kc, rj);
   });
   __syncthreads();
   if constexpr (LV > 0) coarse_adj<NT, M, NL, LV - 1>(A, T, Us);
@@ -562,14 +555,14 @@ __device__ __forceinline__ void coarse_sub(float* __restrict__ sm, int n, int J,
   }
   __syncthreads();
   coarse_an<NT, M, NL, 0>(A, T, Us, k, rho);
-  // coarse plane: U_J <- update with c_J; r_J = U_J
+  // coarse plane: U_J <- update with c_J; r_J = U_J, and A <- r_J - u_{J-1}
   {
     float* UJ = Us + NL * G::NU;
     for (int i = threadIdx.x; i < M * NCH; i += NT) {
       const int c = i % NCH, r = i / NCH;
       const float4 nv = dual4(ld4(UJ + r * P + 4 * c), ld4(A + r * P + 4 * c), k, rho);
       st4(UJ + r * P + 4 * c, nv);
-      st4(A + r * P + 4 * c, nv);
+      st4(A + r * P + 4 * c, sub4(nv, ld4(UJ - G::NU + r * P + 4 * c)));
     }
   }
   __syncthreads();
