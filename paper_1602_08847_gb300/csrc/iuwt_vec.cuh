@@ -219,6 +219,34 @@ struct Region {
   }
 };
 
+// ------------------------------------------------------------------ L2 prefetch for the next wave
+// The one-tile-per-block kernels below run in waves of `ahead` resident
+// blocks.  A block first asks L2 for the inputs of the block `ahead` places
+// later in launch order, the one that takes its place when this wave ends, so
+// that the next wave's first loads find their lines in L2.  (prefetch.global.L2
+// moves no data into the block: a wrong guess costs L2 bandwidth only.)
+__device__ __forceinline__ void pf_line(const float* p) { asm volatile("prefetch.global.L2 [%0];" ::"l"(p)); }
+
+// Linear index of the block `ahead` places later, or -1.
+__device__ __forceinline__ int pf_next(int ahead) {
+  if (ahead <= 0) return -1;
+  const int nb = gridDim.x * gridDim.y * gridDim.z;
+  const int id = blockIdx.x + gridDim.x * (blockIdx.y + gridDim.y * blockIdx.z) + ahead;
+  return id < nb ? id : -1;
+}
+
+// Lines of the region rows ty0 - HY .. ty0 + 63 + HY, columns tx0 - HX ..
+// tx0 + 63 + HX (periodic) of a natural-layout plane.
+template <int NT, int HY, int HX>
+__device__ __forceinline__ void pf_region(const float* __restrict__ plane, int n, int ty0, int tx0) {
+  constexpr int ROWS = kT + 2 * HY, LINES = 2 + 2 * ((HX + 31) / 32);   // tx0 is a multiple of 64
+  const int m = n - 1, q0 = (tx0 - HX) >> 5;
+  for (int i = threadIdx.x; i < ROWS * LINES; i += NT) {
+    const int r = i / LINES, q = i % LINES;
+    pf_line(plane + (size_t)((ty0 - HY + r) & m) * n + ((32 * (q0 + q)) & m));
+  }
+}
+
 // ================================================================== fine analysis (generation 1)
 // Levels j < J1 on a 64 x 64 tile; c_j is needed on a halo HC(j) rows /
 // HX(j) columns (a multiple of 4) around the tile.  A holds c_j in place
@@ -312,12 +340,19 @@ __device__ __forceinline__ void fine_analysis_tile(float* __restrict__ sm, int n
   }
 }
 
-// grid (n/64, n/64, L)
+// grid (n/64, n/64, L); ahead: resident blocks (0: no L2 prefetch)
 template <int NT, int J1>
 __global__ void __launch_bounds__(NT, 2)
 k_fine_analysis_v(int n, int J, const float* __restrict__ D, float* __restrict__ U, float* __restrict__ cr,
-                  float k, float rho) {
+                  float k, float rho, int ahead) {
   extern __shared__ __align__(16) float sm[];
+  const int nx = pf_next(ahead);
+  if (nx >= 0) {
+    const int tx = nx % gridDim.x, ty = (nx / gridDim.x) % gridDim.y, l = nx / (gridDim.x * gridDim.y);
+    const size_t P = (size_t)n * n;
+    pf_region<NT, FineA<J1>::HC(0), FineA<J1>::HX(0)>(D + (size_t)l * P, n, ty * kT, tx * kT);
+    for (int j = 0; j < J1; ++j) pf_region<NT, 0, 0>(U + ((size_t)l * (J + 1) + j) * P, n, ty * kT, tx * kT);
+  }
   fine_analysis_tile<NT, J1>(sm, n, J, D, U, cr, k, rho, blockIdx.z, blockIdx.y * kT, blockIdx.x * kT);
 }
 
@@ -426,8 +461,26 @@ __device__ __forceinline__ void fine_adjoint_tile(float* __restrict__ sm, int n,
 template <int NT, int J1>
 __global__ void __launch_bounds__(NT, 2)
 k_fine_adjoint_v(int n, int J, const float* __restrict__ rin, size_t rin_stride, const float* __restrict__ U,
-                 float* __restrict__ S) {
+                 float* __restrict__ S, int ahead) {
   extern __shared__ __align__(16) float sm[];
+  const int nx = pf_next(ahead);
+  if (nx >= 0) {
+    using G = FineT<J1>;
+    const int tx0 = (nx % gridDim.x) * kT, ty0 = ((nx / gridDim.x) % gridDim.y) * kT, l = nx / (gridDim.x * gridDim.y);
+    const size_t P = (size_t)n * n;
+    pf_region<NT, G::HR(J1), G::HX(J1)>(U + ((size_t)l * (J + 1) + J1 - 1) * P, n, ty0, tx0);
+    // r_J1, class-permuted: per region row and class, the run of sub-columns (two lines at most)
+    constexpr int SC = 1 << J1, HXR = G::HX(J1), NSC = (kT + 2 * HXR) / SC;
+    const int m = n - 1, mc = n >> J1, mm = mc - 1;
+    const size_t mc2 = (size_t)mc * mc;
+    const float* rl = rin + (size_t)l * rin_stride;
+    const int sc0 = (tx0 >> J1) - HXR / SC;
+    for (int i = threadIdx.x; i < G::RA * SC * 2; i += NT) {
+      const int e = i & 1, cx = (i >> 1) % SC, r = (i >> 1) / SC;
+      const int gy = (ty0 - G::HR(J1) + r) & m;
+      pf_line(rl + (size_t)((gy & (SC - 1)) * SC + cx) * mc2 + (size_t)(gy >> J1) * mc + ((sc0 + e * (NSC - 1)) & mm));
+    }
+  }
   fine_adjoint_tile<NT, J1>(sm, n, J, rin, rin_stride, U, S, blockIdx.z, blockIdx.y * kT, blockIdx.x * kT);
 }
 
@@ -581,8 +634,18 @@ __device__ __forceinline__ void coarse_sub(float* __restrict__ sm, int n, int J,
 template <int NT, int M, int NL>
 __global__ void __launch_bounds__(NT, 2)
 k_coarse_v(int n, int J, int j1, const float* __restrict__ c_in, float* __restrict__ r_out, float* __restrict__ U,
-           float k, float rho) {
+           float k, float rho, int ahead) {
   extern __shared__ __align__(16) float sm[];
+  const int nx = pf_next(ahead);
+  if (nx >= 0) {
+    const int cls = nx % gridDim.x, l = nx / gridDim.x;
+    const size_t Pl = (size_t)n * n, sub = (size_t)cls * M * M;
+    for (int i = threadIdx.x; i < (NL + 2) * (M * M / 32); i += NT) {
+      const int pl = i / (M * M / 32), q = i % (M * M / 32);
+      const float* base = pl == 0 ? c_in + (size_t)l * Pl : U + ((size_t)l * (J + 1) + j1 + pl - 1) * Pl;
+      pf_line(base + sub + 32 * q);
+    }
+  }
   coarse_sub<NT, M, NL>(sm, n, J, j1, c_in, r_out, U, k, rho, blockIdx.x, blockIdx.y);
 }
 
