@@ -28,6 +28,23 @@ inline cudaError_t allow_max_dyn_smem(F* fn) {
   return cudaFuncSetAttribute(fn, cudaFuncAttributePreferredSharedMemoryCarveout, (int)cudaSharedmemCarveoutMaxShared);
 }
 
+// ----------------------------------------------------------------- L2 prefetch for the next wave
+// Kernels that run one tile per block run in waves of `ahead` resident blocks
+// (host: resident_blocks, internal.h).  A block first asks L2 for the inputs
+// of the block `ahead` places later in launch order, the one that takes its
+// place when this wave ends, so that the next wave's first loads find their
+// lines in L2.  prefetch.global.L2 moves no data into the block: a wrong guess
+// costs L2 bandwidth only.
+__device__ __forceinline__ void pf_line(const float* p) { asm volatile("prefetch.global.L2 [%0];" ::"l"(p)); }
+
+// Linear index of the block `ahead` places later in launch order, or -1.
+__device__ __forceinline__ int pf_next(int ahead) {
+  if (ahead <= 0) return -1;
+  const int nb = gridDim.x * gridDim.y * gridDim.z;
+  const int id = blockIdx.x + gridDim.x * (blockIdx.y + gridDim.y * blockIdx.z) + ahead;
+  return id < nb ? id : -1;
+}
+
 // ----------------------------------------------------------------- complex
 template <typename T> struct __align__(2 * sizeof(T)) cpx { T x, y; };
 

@@ -4,6 +4,10 @@
 #include <stddef.h>
 #include <stdint.h>
 
+#include <cstdlib>
+#include <map>
+#include <mutex>
+
 namespace muffin {
 
 // Geometry of one cube as the kernels see it.
@@ -177,5 +181,28 @@ cudaError_t launch_fill_random(float* x, size_t n, uint64_t seed, cudaStream_t s
 cudaError_t launch_permute_planes(const float* src, float* dst, int n, int L, int J, int j1, int to_class,
                                   cudaStream_t s);
 cudaError_t launch_nonfinite_count(const float* x, size_t n, int* count, cudaStream_t s);
+
+// Blocks of kernel fn resident on the device at once: how far ahead in launch
+// order a block prefetches inputs into L2 (0 with MUFFIN_L2_PREFETCH=0).
+template <typename F>
+inline int resident_blocks(F* fn, int nt, size_t smem) {
+  static std::mutex mu;
+  static std::map<const void*, int> known;
+  static const bool on = [] {
+    const char* e = getenv("MUFFIN_L2_PREFETCH");
+    return !(e && atoi(e) == 0);
+  }();
+  if (!on) return 0;
+  std::lock_guard<std::mutex> lk(mu);
+  const auto it = known.find(reinterpret_cast<const void*>(fn));
+  if (it != known.end()) return it->second;
+  int dev = 0, sms = 0, occ = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fn, nt, smem) != cudaSuccess) {
+    cudaGetLastError();
+    return 0;
+  }
+  return known[reinterpret_cast<const void*>(fn)] = sms * occ;
+}
 
 }  // namespace muffin

@@ -220,21 +220,7 @@ struct Region {
 };
 
 // ------------------------------------------------------------------ L2 prefetch for the next wave
-// The one-tile-per-block kernels below run in waves of `ahead` resident
-// blocks.  A block first asks L2 for the inputs of the block `ahead` places
-// later in launch order, the one that takes its place when this wave ends, so
-// that the next wave's first loads find their lines in L2.  (prefetch.global.L2
-// moves no data into the block: a wrong guess costs L2 bandwidth only.)
-__device__ __forceinline__ void pf_line(const float* p) { asm volatile("prefetch.global.L2 [%0];" ::"l"(p)); }
-
-// Linear index of the block `ahead` places later, or -1.
-__device__ __forceinline__ int pf_next(int ahead) {
-  if (ahead <= 0) return -1;
-  const int nb = gridDim.x * gridDim.y * gridDim.z;
-  const int id = blockIdx.x + gridDim.x * (blockIdx.y + gridDim.y * blockIdx.z) + ahead;
-  return id < nb ? id : -1;
-}
-
+// (pf_line, pf_next: device.cuh)
 // Lines of the region rows ty0 - HY .. ty0 + 63 + HY, columns tx0 - HX ..
 // tx0 + 63 + HX (periodic) of a natural-layout plane.
 template <int NT, int HY, int HX>
@@ -458,6 +444,15 @@ __device__ __forceinline__ void fine_adjoint_tile(float* __restrict__ sm, int n,
   }
 }
 
+// u_{J0-1} on halo HR(J0) for J0 = J1-1 .. 1: what the levels load as they go.
+template <int NT, int J1, int J0>
+__device__ __forceinline__ void pf_adj_planes(const float* __restrict__ Ul, size_t P, int n, int ty0, int tx0) {
+  if constexpr (J0 >= 1) {
+    pf_region<NT, FineT<J1>::HR(J0), FineT<J1>::HX(J0)>(Ul + (size_t)(J0 - 1) * P, n, ty0, tx0);
+    pf_adj_planes<NT, J1, J0 - 1>(Ul, P, n, ty0, tx0);
+  }
+}
+
 template <int NT, int J1>
 __global__ void __launch_bounds__(NT, 2)
 k_fine_adjoint_v(int n, int J, const float* __restrict__ rin, size_t rin_stride, const float* __restrict__ U,
@@ -469,6 +464,7 @@ k_fine_adjoint_v(int n, int J, const float* __restrict__ rin, size_t rin_stride,
     const int tx0 = (nx % gridDim.x) * kT, ty0 = ((nx / gridDim.x) % gridDim.y) * kT, l = nx / (gridDim.x * gridDim.y);
     const size_t P = (size_t)n * n;
     pf_region<NT, G::HR(J1), G::HX(J1)>(U + ((size_t)l * (J + 1) + J1 - 1) * P, n, ty0, tx0);
+    pf_adj_planes<NT, J1, J1 - 1>(U + (size_t)l * (J + 1) * P, P, n, ty0, tx0);
     // r_J1, class-permuted: per region row and class, the run of sub-columns (two lines at most)
     constexpr int SC = 1 << J1, HXR = G::HX(J1), NSC = (kT + 2 * HXR) / SC;
     const int m = n - 1, mc = n >> J1, mm = mc - 1;

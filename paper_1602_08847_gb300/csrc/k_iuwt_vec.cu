@@ -1,7 +1,5 @@
 // Host launchers of the vectorised generation-1 IUWT kernels (iuwt_vec.cuh).
 #include <cstdlib>
-#include <map>
-#include <mutex>
 
 #include "internal.h"
 #include "iuwt_vec.cuh"
@@ -19,35 +17,12 @@ bool iuwt_vec_coarse_ok(const Geom& g) {
 // Threads per block of the fine and of the coarse kernels: g.fnt / g.cnt,
 // 256 (two blocks per SM) or 512, chosen by the set-up autotuner.
 
-// Blocks of kernel fn resident on the device at once: how far ahead in launch
-// order a block prefetches inputs into L2 (0 with MUFFIN_L2_PREFETCH=0).
-template <typename F>
-static int ahead_of(F* fn, int nt, size_t smem) {
-  static std::mutex mu;
-  static std::map<const void*, int> known;
-  static const bool on = [] {
-    const char* e = getenv("MUFFIN_L2_PREFETCH");
-    return !(e && atoi(e) == 0);
-  }();
-  if (!on) return 0;
-  std::lock_guard<std::mutex> lk(mu);
-  const auto it = known.find(reinterpret_cast<const void*>(fn));
-  if (it != known.end()) return it->second;
-  int dev = 0, sms = 0, occ = 0;
-  if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
-      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fn, nt, smem) != cudaSuccess) {
-    cudaGetLastError();
-    return 0;
-  }
-  return known[reinterpret_cast<const void*>(fn)] = sms * occ;
-}
-
 template <int NT>
 static cudaError_t fine_an_vec(const Geom& g, const IuwtArgs& a, cudaStream_t s) {
   dim3 grid(g.n / vec::kT, g.n / vec::kT, g.L);
 #define FA(JJ)                                                                                          \
   vec::k_fine_analysis_v<NT, JJ><<<grid, NT, vec::FineA<JJ>::SMEM, s>>>(                                \
-      g.n, g.J, a.D, a.U, a.cr, a.k, a.rho, ahead_of(vec::k_fine_analysis_v<NT, JJ>, NT, vec::FineA<JJ>::SMEM))
+      g.n, g.J, a.D, a.U, a.cr, a.k, a.rho, resident_blocks(vec::k_fine_analysis_v<NT, JJ>, NT, vec::FineA<JJ>::SMEM))
   switch (g.j1) {
     case 1: FA(1); break;
     case 2: FA(2); break;
@@ -71,7 +46,7 @@ static cudaError_t fine_adj_vec(const Geom& g, const IuwtArgs& a, cudaStream_t s
   const size_t stride = from_u ? (size_t)(g.J + 1) * P : P;
 #define FT(JJ)                                                                                     \
   vec::k_fine_adjoint_v<NT, JJ><<<grid, NT, vec::FineT<JJ>::SMEM, s>>>(                            \
-      g.n, g.J, rin, stride, a.U, a.S, ahead_of(vec::k_fine_adjoint_v<NT, JJ>, NT, vec::FineT<JJ>::SMEM))
+      g.n, g.J, rin, stride, a.U, a.S, resident_blocks(vec::k_fine_adjoint_v<NT, JJ>, NT, vec::FineT<JJ>::SMEM))
   switch (g.j1) {
     case 1: FT(1); break;
     case 2: FT(2); break;
@@ -95,7 +70,7 @@ static cudaError_t coarse_vec(const Geom& g, const float* c_in, float* r_out, fl
   if (M == MM && NL == LL) {                                                                                   \
     vec::k_coarse_v<NT, MM, LL><<<grid, NT, vec::CoarseV<MM, LL>::SMEM, s>>>(                              \
         g.n, g.J, g.j1, c_in, r_out, U, k, rho,                                                            \
-        ahead_of(vec::k_coarse_v<NT, MM, LL>, NT, vec::CoarseV<MM, LL>::SMEM));                             \
+        resident_blocks(vec::k_coarse_v<NT, MM, LL>, NT, vec::CoarseV<MM, LL>::SMEM));                             \
     return cudaGetLastError();                                                                                 \
   }
   CV(32, 1) CV(32, 2) CV(32, 3) CV(64, 1) CV(64, 2) CV(64, 3)
