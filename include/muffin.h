@@ -221,7 +221,7 @@ void muffin_batch_destroy(muffin_batch* batch);
  * library holds until the process exits.  Limits: 1 <= n_pix <= 2^20,
  * 1 <= nchan <= 256; larger sizes return MUFFIN_ERR_ARG.  Calls no cudaMalloc
  * or cudaFree.  The first call on each device looks up the array's device
- * address (make that first call before any stream capture).  Every call
+ * address.  Every call
  * shares the array and leaves its contents behind, so calls that overlap on
  * the GPU (other streams, other host threads) race: serialise them.
  * Asynchronous on stream; errors are described by muffin_noalloc_last_error. */
