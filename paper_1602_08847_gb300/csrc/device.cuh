@@ -37,6 +37,14 @@ inline cudaError_t allow_max_dyn_smem(F* fn) {
 // costs L2 bandwidth only.
 __device__ __forceinline__ void pf_line(const float* p) { asm volatile("prefetch.global.L2 [%0];" ::"l"(p)); }
 
+// A contiguous run of `bytes` (a multiple of 16; p 16-byte aligned) into L2 with
+// one bulk prefetch.  (Worth it for long runs: the coarse kernel's 16 KB
+// sub-images.  Row-sized runs of the fine kernels measured slower this way than
+// as per-line prefetches.)
+__device__ __forceinline__ void pf_bulk(const float* p, unsigned bytes) {
+  asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(p), "r"(bytes) : "memory");
+}
+
 // Linear index of the block `ahead` places later in launch order, or -1.
 __device__ __forceinline__ int pf_next(int ahead) {
   if (ahead <= 0) return -1;

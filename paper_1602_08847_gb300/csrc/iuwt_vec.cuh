@@ -220,7 +220,7 @@ struct Region {
 };
 
 // ------------------------------------------------------------------ L2 prefetch for the next wave
-// (pf_line, pf_next: device.cuh)
+// (pf_line, pf_bulk, pf_next: device.cuh)
 // Lines of the region rows ty0 - HY .. ty0 + 63 + HY, columns tx0 - HX ..
 // tx0 + 63 + HX (periodic) of a natural-layout plane.
 template <int NT, int HY, int HX>
@@ -636,10 +636,12 @@ k_coarse_v(int n, int J, int j1, const float* __restrict__ c_in, float* __restri
   if (nx >= 0) {
     const int cls = nx % gridDim.x, l = nx / gridDim.x;
     const size_t Pl = (size_t)n * n, sub = (size_t)cls * M * M;
-    for (int i = threadIdx.x; i < (NL + 2) * (M * M / 32); i += NT) {
-      const int pl = i / (M * M / 32), q = i % (M * M / 32);
+    // c_j1 and U_j1..U_J of the sub-image: NL + 2 contiguous runs of M^2 floats,
+    // one bulk prefetch each
+    if (threadIdx.x < NL + 2) {
+      const int pl = threadIdx.x;
       const float* base = pl == 0 ? c_in + (size_t)l * Pl : U + ((size_t)l * (J + 1) + j1 + pl - 1) * Pl;
-      pf_line(base + sub + 32 * q);
+      pf_bulk(base + sub, 4u * M * M);
     }
   }
   coarse_sub<NT, M, NL>(sm, n, J, j1, c_in, r_out, U, k, rho, blockIdx.x, blockIdx.y);
