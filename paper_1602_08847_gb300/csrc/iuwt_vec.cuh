@@ -403,34 +403,50 @@ __device__ __forceinline__ void fine_adjoint_tile(float* __restrict__ sm, int n,
   {
     Region<NT, G::HR(J1), G::HX(J1), G::PA> ub;
     ub.load(Uc, n, ty0, tx0);
-    // r_J1 region from the class-permuted plane: per (row, class) runs of
-    // sub-columns read two at a time (8-byte aligned), scattered into R
+    // r_J1 region from the class-permuted plane, read two sub-columns (8 bytes)
+    // at a time and scattered into R.  Lane (cx, p) of a warp takes class cx
+    // and sub-column pairs p, p + PL, ... of the warp's rows (rows wid,
+    // wid + NW, ...): per row one address computation; a warp's load is eight
+    // 32-byte runs.  Lanes in the upper half of p write the odd sub-column
+    // first, which puts the two halves of the warp on different banks.
     constexpr int SC = 1 << J1, HXR = G::HX(J1), NSC = (kT + 2 * HXR) / SC, NP = NSC / 2;
+    constexpr int PL = 32 / SC, NPP = (NP + PL - 1) / PL;
+    constexpr int NW = NT / 32, RPW = (G::RA + NW - 1) / NW;
     const int mc = n >> J1, mm = mc - 1, m = n - 1;
     const size_t mc2 = (size_t)mc * mc;
     const float* rl = rin + (size_t)l * rin_stride;
     const int sc0 = (tx0 >> J1) - HXR / SC;
-    constexpr int NR = G::RA * SC * NP, NRT = (NR + NT - 1) / NT;
-    float2 rv[NRT];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    const int cx = lane % SC, p = lane / SC;
+    float2 rv[RPW][NPP];
 #pragma unroll
-    for (int q = 0; q < NRT; ++q) {        // every load in flight before the first store
-      const int i = threadIdx.x + q * NT;
-      if (i < NR) {
-        const int cx = i % SC, rest = i / SC, p2 = rest % NP, r = rest / NP;
+    for (int rr = 0; rr < RPW; ++rr) {     // every load in flight before the first store
+      const int r = wid + rr * NW;
+      if (r < G::RA) {
         const int gy = (ty0 - G::HR(J1) + r) & m;
-        const int sc = (sc0 + 2 * p2) & mm;
-        rv[q] = __ldcg(reinterpret_cast<const float2*>(rl + (size_t)((gy & (SC - 1)) * SC + cx) * mc2 +
-                                                      (size_t)(gy >> J1) * mc + sc));
+        const float* row = rl + (size_t)((gy & (SC - 1)) * SC + cx) * mc2 + (size_t)(gy >> J1) * mc;
+#pragma unroll
+        for (int h = 0; h < NPP; ++h) {
+          const int p2 = p + h * PL;
+          if (p2 < NP) rv[rr][h] = __ldcg(reinterpret_cast<const float2*>(row + ((sc0 + 2 * p2) & mm)));
+        }
       }
     }
+    const bool odd_first = p >= PL / 2;
 #pragma unroll
-    for (int q = 0; q < NRT; ++q) {
-      const int i = threadIdx.x + q * NT;
-      if (i < NR) {
-        const int cx = i % SC, rest = i / SC, p2 = rest % NP, r = rest / NP;
-        float* d = R + r * G::PA + cx + SC * 2 * p2;
-        d[0] = rv[q].x;
-        d[SC] = rv[q].y;
+    for (int rr = 0; rr < RPW; ++rr) {
+      const int r = wid + rr * NW;
+      if (r < G::RA) {
+#pragma unroll
+        for (int h = 0; h < NPP; ++h) {
+          const int p2 = p + h * PL;
+          if (p2 < NP) {
+            float* d = R + r * G::PA + cx + SC * 2 * p2;
+            const float2 v = rv[rr][h];
+            d[odd_first ? SC : 0] = odd_first ? v.y : v.x;
+            d[odd_first ? 0 : SC] = odd_first ? v.x : v.y;
+          }
+        }
       }
     }
     ub.template store<0, 0>(Ub);
