@@ -316,7 +316,11 @@ __device__ __forceinline__ void fine_analysis_tile(float* __restrict__ sm, int n
   const size_t mc2 = (size_t)mc * mc;
   float* dst = J == J1 ? U + ((size_t)l * (J + 1) + J) * P : cr + (size_t)l * P;
   for (int i = threadIdx.x; i < kT * S * NSUB; i += NT) {
-    const int cx = i % S, rest = i / S, m4 = rest % NSUB, r = rest / NSUB;
+    // at S = 8 the rows are taken in the order 0, 2, 1, 3 of each group of four:
+    // the two rows of a warp then sit 2 pitches apart, which halves the bank
+    // conflicts of the strided reads (4-way -> 2-way)
+    const int cx = i % S, rest = i / S, m4 = rest % NSUB, rr = rest / NSUB;
+    const int r = S == 8 ? (rr & ~3) | ((rr & 1) << 1) | ((rr >> 1) & 1) : rr;
     const float* a = A + (G::HC(0) + r) * G::PA + G::HX(0) + cx + S * 4 * m4;
     float4 v = make_float4(a[0], a[S], a[2 * S], a[3 * S]);
     const int gy = ty0 + r;
