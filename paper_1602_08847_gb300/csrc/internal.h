@@ -182,17 +182,19 @@ cudaError_t launch_permute_planes(const float* src, float* dst, int n, int L, in
                                   cudaStream_t s);
 cudaError_t launch_nonfinite_count(const float* x, size_t n, int* count, cudaStream_t s);
 
-// Blocks of kernel fn resident on the device at once: how far ahead in launch
-// order a block prefetches inputs into L2 (0 with MUFFIN_L2_PREFETCH=0).
+// How far ahead in launch order a block prefetches inputs into L2: the blocks
+// of kernel fn resident on the device at once (one wave), times
+// MUFFIN_L2_PREFETCH when that is set (0: no prefetch; 2: two waves ahead).
 template <typename F>
 inline int resident_blocks(F* fn, int nt, size_t smem) {
   static std::mutex mu;
   static std::map<const void*, int> known;
-  static const bool on = [] {
+  static const int waves = [] {
     const char* e = getenv("MUFFIN_L2_PREFETCH");
-    return !(e && atoi(e) == 0);
+    const int w = e ? atoi(e) : 1;
+    return w < 0 ? 0 : (w > 4 ? 4 : w);
   }();
-  if (!on) return 0;
+  if (waves == 0) return 0;
   std::lock_guard<std::mutex> lk(mu);
   const auto it = known.find(reinterpret_cast<const void*>(fn));
   if (it != known.end()) return it->second;
@@ -202,7 +204,7 @@ inline int resident_blocks(F* fn, int nt, size_t smem) {
     cudaGetLastError();
     return 0;
   }
-  return known[reinterpret_cast<const void*>(fn)] = sms * occ;
+  return known[reinterpret_cast<const void*>(fn)] = sms * occ * waves;
 }
 
 }  // namespace muffin
